@@ -1,0 +1,234 @@
+/*
+ * refusion.h -- C ABI of the GB300 (sm_103a) ReFusion per-frame hot path.
+ *
+ * ReFusion (Palazzolo, Behley, Lottes, Giguere, Stachniss; IROS 2019) tracks
+ * an RGB-D camera directly against a voxel-hashed TSDF with an SDF + colour
+ * error (Sec. III-B, Eq. 1-4), detects dynamic pixels from the registration
+ * residuals (Sec. III-C, Eq. 5, Alg. 1), registers again without them and
+ * integrates the masked frame with explicit free-space carving (Sec. III-A,
+ * III-D).  This library runs that loop in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ *  - Plain C types only.  `stream` is a cudaStream_t passed as void* (NULL =
+ *    the legacy default stream).  Calls taking device pointers enqueue work on
+ *    `stream` and return without synchronising; they are stream-ordered with
+ *    respect to the caller's other work on that stream.
+ *  - A pose T is a row-major 4x4 double matrix mapping camera coordinates to
+ *    world coordinates (Eq. 2 applies T to back-projected camera points).
+ *    Camera frame: x right, y down, z forward (pinhole, Eq. 1).
+ *  - Depth: uint16, row-major, width*height, in units of 1/depth_scale metres;
+ *    0 = invalid (Sec. III-E, first option).  Colour: RGB8 interleaved,
+ *    width*height*3 bytes.  Masks: uint8 per pixel, nonzero = dynamic.
+ *  - Ownership: the library owns every buffer it allocates (all inside
+ *    rf_create_volume); caller buffers are borrowed for the duration of the
+ *    enqueued work only.  No call allocates device memory after creation,
+ *    except rf_volume_export/import staging on the host.
+ *  - Errors: each call returns an rf_status.  Argument errors are detected on
+ *    the host before anything is enqueued.  Errors found by kernels (hash or
+ *    pool full, candidate overflow, flood fill not converged, barrier timeout)
+ *    are OR-ed into a per-volume device status word; rf_sync_status()
+ *    synchronises the stream, returns the first such error and clears it.
+ *    rf_last_error() gives a readable message for the last failing call.
+ *  - Every device loop is bounded; no kernel traps or spins without a limit.
+ *  - A volume is not thread-safe: use one host thread (and one stream) per
+ *    volume at a time.  Independent volumes may run concurrently.
+ */
+#ifndef REFUSION_H
+#define REFUSION_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RF_ABI_VERSION 1
+
+typedef enum rf_status {
+  RF_OK = 0,
+  RF_ERR_INVALID_ARG = 1,      /* bad pointer, size or parameter */
+  RF_ERR_CUDA = 2,             /* a CUDA runtime call failed (message in rf_last_error) */
+  RF_ERR_HASH_FULL = 3,        /* bounded hash probe found no free slot */
+  RF_ERR_POOL_FULL = 4,        /* more blocks than max_blocks */
+  RF_ERR_NOT_CONVERGED = 5,    /* flood fill exceeded max_ff_sweeps, or a grid barrier timed out */
+  RF_ERR_BUFFER_TOO_SMALL = 6, /* caller buffer smaller than the result */
+  RF_ERR_OUT_OF_RANGE = 7,     /* block coordinate outside +-8191 blocks per axis */
+  RF_ERR_CAPACITY = 8          /* frustum candidate list overflow (raise max_candidates) */
+} rf_status;
+
+/* Parameters.  Defaults (rf_default_params) are Tab. I of the paper (voxel
+ * 0.01 m, tau 0.1 m, w_c 0.025, theta 0.007, gamma 0.5) and the readings
+ * for the quantities the paper leaves open. */
+typedef struct rf_params {
+  double voxel_size;   /* metres; voxel_size * 1e6 must be an integer (micrometre lattice) */
+  double trunc;        /* truncation distance tau (Sec. III-A), metres */
+  double w_c;          /* colour weight w_c of Eq. 4 */
+  double theta;        /* flood-fill depth threshold of Alg. 1 (used as round(theta*1e6) ppm) */
+  double gamma;        /* residual threshold weight of Eq. 5, t = gamma tau^2 */
+  double depth_scale;  /* raw depth units per metre; 1e6/depth_scale must be an integer */
+  double d_min;        /* valid depth range [d_min, d_max], metres */
+  double d_max;        /* also the carving clipping plane (Sec. III-D); <= 50 m */
+  double z_near;       /* near plane of the carved frustum, metres (> 0) */
+  int w_max;           /* cap of the SDF and colour weights, 1..255 */
+  int lm_iters[3];     /* LM candidate evaluations per level (coarse to fine) */
+  int lm_strides[3];   /* pixel sub-sampling stride per level (Sec. III-B: 3 sub-samplings) */
+  double lm_lambda0;   /* initial Marquardt damping */
+  double lm_eps_trans; /* level converged when |delta rho| < eps_trans (m) ... */
+  double lm_eps_rot;   /* ... and |delta phi| < eps_rot (rad) */
+  int lm_min_valid;    /* an evaluation with fewer valid pixels is rejected */
+  int max_ff_sweeps;   /* bound on flood-fill sweeps (RF_ERR_NOT_CONVERGED beyond) */
+  int64_t max_candidates; /* capacity of the per-frame frustum block candidate list */
+} rf_params;
+
+/* One RGB-D frame in device memory (row-major, rows of exactly `width`). */
+typedef struct rf_frame {
+  int height, width;
+  double fx, fy, cx, cy;   /* pinhole intrinsics (Eq. 1); fx*256 and (cx+0.5)*256 are rounded to integers */
+  const uint16_t* depth;   /* device, height*width */
+  const uint8_t* rgb;      /* device, height*width*3 */
+} rf_frame;
+
+/* Registration summary (written to device memory by rf_track_frame). */
+typedef struct rf_track_info {
+  int evals;            /* cost evaluations over the three levels */
+  int level_evals[3];
+  int converged[3];     /* 1 if the level stopped on the step-size test or a failed solve */
+  double final_cost;    /* mean cost E/N at the returned pose, last evaluated level */
+  int64_t final_valid;  /* N: pixels with a valid model lookup at that evaluation */
+} rf_track_info;
+
+typedef struct rf_stats {
+  int64_t n_blocks;       /* allocated 8x8x8 voxel blocks */
+  int64_t max_blocks;
+  int64_t n_buckets;      /* hash buckets (4 slots each) */
+  int64_t frames;         /* frames processed by rf_process_frame */
+  double load_factor;     /* n_blocks / (4 n_buckets) */
+  int64_t device_bytes;   /* device memory owned by the volume */
+} rf_stats;
+
+/* Device-side timings and work counters of the last frame (rf_get_profile). */
+typedef struct rf_profile {
+  float frame_ms;            /* device time of the last rf_process_frame* call */
+  float track_ms[2];         /* first and second registration */
+  float mask_ms;             /* seeds, erosion, flood fill, dilation */
+  float integrate_ms;        /* integration stage: pose quantisation, tile maxima, frustum, cull, update */
+  float integrate_kernel_ms; /* the per-voxel update kernel alone */
+  int64_t candidates;        /* frustum candidate blocks of the last integration */
+  int64_t updated_voxels;    /* voxels updated by the last integration */
+  int64_t new_blocks;        /* blocks allocated by the last integration */
+  int64_t guard_pixels;      /* mask seeds decided by the FP64 re-evaluation in the last mask */
+} rf_profile;
+
+typedef struct rf_volume rf_volume;
+
+/* Fills `p` with the defaults described above.  Never fails for p != NULL. */
+rf_status rf_default_params(rf_params* p);
+
+/* Creates a voxel-hashed TSDF volume on the current CUDA device (Sec. III-A:
+ * blocks allocated on demand, indexed by a spatial hash).  n_buckets must be
+ * a power of two (4 slots per bucket); max_blocks <= 4,194,302.  max_width and
+ * max_height bound the frames this volume accepts (per-frame scratch is sized
+ * from them).  All device memory is allocated here.  On error *out is NULL. */
+rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width,
+                           int max_height, rf_volume** out);
+
+/* Synchronises the device and frees everything the volume owns.  NULL is a no-op. */
+rf_status rf_destroy_volume(rf_volume* vol);
+
+/* Empties the volume (all blocks freed, frame counter 0); synchronous. */
+rf_status rf_volume_reset(rf_volume* vol);
+
+/* Levenberg-Marquardt registration of a frame against the model (Sec. III-B):
+ * minimises E = sum V_SDF(exp(xi) T x_i)^2 + w_c sum (V_I(exp(xi) T x_i) - I(p_i))^2
+ * (Eq. 2-4) over the pixel strides lm_strides, starting at *T_init_dev.
+ * mask_dev (device, nullable): pixels with nonzero mask are excluded (the
+ * second registration of Sec. III-C).  T_init_dev/T_out_dev: device double[16]
+ * (may alias).  info_dev: device rf_track_info or NULL.  Asynchronous. */
+rf_status rf_track_frame(rf_volume* vol, const rf_frame* frame, const double* T_init_dev, const uint8_t* mask_dev,
+                         double* T_out_dev, rf_track_info* info_dev, void* stream);
+
+/* Dynamic mask at pose *T_dev (Sec. III-C): residual r_i = V_SDF(T x_i)^2
+ * (Eq. 2), seeds r_i > gamma tau^2 (Eq. 5), 3x3 erosion, the depth-aware
+ * flood fill of Alg. 1 (4-neighbours, |D(p)-D(n)| < theta D(p)), 3x3
+ * dilation.  mask_dev: device uint8 height*width (caller-owned output).
+ * Seeds are decided exactly: near the threshold the residual is re-evaluated
+ * in FP64 in a fixed operation order.  Asynchronous. */
+rf_status rf_compute_mask(rf_volume* vol, const rf_frame* frame, const double* T_dev, uint8_t* mask_dev,
+                          void* stream);
+
+/* Integrates the frame at pose *T_dev (Sec. III-A running weighted average,
+ * Sec. III-D free-space carving): every voxel projecting to a valid, unmasked
+ * pixel with z in (z_near, d_max] and sdf = D - z >= -tau is updated with
+ * sdf (|sdf| <= tau, colour too) or with tau (sdf > tau: free space).  Blocks
+ * holding at least one such voxel are allocated.  Discrete decisions use exact
+ * integer arithmetic.  mask_dev nullable.  Asynchronous. */
+rf_status rf_integrate_frame(rf_volume* vol, const rf_frame* frame, const double* T_dev, const uint8_t* mask_dev,
+                             void* stream);
+
+/* The whole per-frame loop (Fig. 2 / Sec. III-C): track -> mask -> track
+ * without masked pixels -> integrate with that pose and mask.  The first frame
+ * of a volume is integrated at *T_init_dev without tracking.  Device pointers:
+ * T_init_dev (in), T_out_dev (out), mask_dev (out, nullable), info_dev (out,
+ * nullable; info of the second registration).  The frame is copied into
+ * volume-owned staging buffers first, so the caller may reuse its buffers once
+ * the stream passes this call.  The device work is replayed from a CUDA graph
+ * captured per (frame size, intrinsics, first-frame) combination.
+ * Asynchronous. */
+rf_status rf_process_frame(rf_volume* vol, const rf_frame* frame, const double* T_init_dev, double* T_out_dev,
+                           uint8_t* mask_dev, rf_track_info* info_dev, void* stream);
+
+/* Same loop from HOST buffers: copies depth/rgb/T_init to the device, runs
+ * rf_process_frame, copies the pose (and the mask if mask_host != NULL) back
+ * and synchronises the stream.  Returns kernel-detected errors too.
+ * intrinsics = {fx, fy, cx, cy}. */
+rf_status rf_process_frame_host(rf_volume* vol, int height, int width, const double intrinsics[4],
+                                const uint16_t* depth_host, const uint8_t* rgb_host, const double T_init_host[16],
+                                double T_out_host[16], uint8_t* mask_host, void* stream);
+
+/* Zero-crossing surface of the TSDF (the mesh of Sec. I) by marching
+ * tetrahedra over cells whose 8 corners are observed; triangle soup, normals
+ * towards positive SDF.  verts_dev: float [cap_tris][3][3]; colors_dev: uint8
+ * [cap_tris][3][3].  With verts_dev == NULL only *n_tris_host is computed.
+ * Synchronises `stream` (the count is returned on the host).
+ * RF_ERR_BUFFER_TOO_SMALL if the mesh has more than cap_tris triangles. */
+rf_status rf_extract_mesh(rf_volume* vol, float* verts_dev, uint8_t* colors_dev, int64_t cap_tris,
+                          int64_t* n_tris_host, void* stream);
+
+/* Host snapshot of the volume, blocks sorted by (bz, by, bx); voxel index
+ * x + 8y + 64z.  coords int32 [n][3]; F float [n][512] (0 where W = 0);
+ * W, wc uint8 [n][512] (SDF and colour weights); rgb uint8 [n][512][3].
+ * With coords == NULL only *n_blocks is returned.  Synchronous. */
+rf_status rf_volume_export(rf_volume* vol, int64_t cap_blocks, int32_t* coords, float* F, uint8_t* W,
+                           uint8_t* rgb, uint8_t* wc, int64_t* n_blocks);
+
+/* Replaces the volume content with a host snapshot in the export layout.
+ * Synchronous. */
+rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coords, const float* F,
+                           const uint8_t* W, const uint8_t* rgb, const uint8_t* wc);
+
+rf_status rf_volume_stats(rf_volume* vol, rf_stats* out);
+
+/* Enables (1) or disables (0) device timing of the whole-frame calls: CUDA
+ * events recorded on the caller's stream (kept inside the captured graphs)
+ * around each stage and around the per-voxel update kernel.  Work counters
+ * are always kept.  Takes effect for the next frame. */
+rf_status rf_set_profiling(rf_volume* vol, int enable);
+
+/* Synchronises `stream` and returns the timings (if profiling is enabled;
+ * zeros otherwise) and the work counters of the last frame. */
+rf_status rf_get_profile(rf_volume* vol, void* stream, rf_profile* out);
+
+/* Synchronises `stream`, returns the first kernel-detected error since the
+ * last call (RF_OK if none) and clears the device status word. */
+rf_status rf_sync_status(rf_volume* vol, void* stream);
+
+/* Message of the last failing call on this volume (vol == NULL: last
+ * creation error).  The string stays valid until the next call. */
+const char* rf_last_error(rf_volume* vol);
+
+const char* rf_status_string(rf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REFUSION_H */

@@ -34,8 +34,9 @@
 //   * a block is allocated when at least one of its voxels is updated;
 //   * weights count observations (1 each), capped at w_max; colour has its
 //     own weight and is stored as RGB8, rounded half up at every update;
-//   * the residual of the mask is V_SDF^2 (the underbraced term of Eq. 2) and
-//     seeds are r_i > t; erosion/dilation are 3x3 squares (outside = 0);
+//   * the residual of the mask is V_SDF^2 (the underbraced term of Eq. 2),
+//     V_SDF clamped to [-tau, tau] (the TSDF is truncated at tau), and seeds
+//     are r_i > t; erosion/dilation are 3x3 squares (outside = 0);
 //     Alg. 1 uses 4-neighbours and the test |D(p)-D(n)| 1e6 < theta_ppm D(p)
 //     on raw integer depth;
 //   * LM: H + lambda diag(H), lambda0 = 1e-4, /10 on accept, x10 on reject,
@@ -557,7 +558,8 @@ void residual_seeds(Volume& V, const orc_frame* f, const double T[16], double* r
         double fr[3];
         Corners c;
         if (cell_of(V, p, k0, fr) && gather(V, k0, &c)) {
-          double sdf = trilinear(c.F, fr);
+          // the model is a TSDF truncated at tau (Sec. III-A)
+          double sdf = std::min(std::max(trilinear(c.F, fr), -V.p.trunc), V.p.trunc);
           ri = sdf * sdf;  // r_i of Eq. 2
         }
       }

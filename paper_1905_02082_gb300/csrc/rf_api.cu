@@ -1,0 +1,686 @@
+// C entry points of refusion.h: volume lifecycle, argument checking, error
+// reporting, snapshots and the whole-frame pipeline (ReFusion Fig. 2:
+// track -> mask -> track without masked pixels -> integrate), which is
+// captured once per frame geometry into a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "rf_volume.hpp"
+
+namespace rf {
+int floodfill_max_grid(int device);
+
+static thread_local std::string g_create_error;
+
+rf_status set_error(rf_volume* vol, rf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (vol) vol->last_error = buf;
+  else g_create_error = buf;
+  return s;
+}
+
+rf_status check_cuda(rf_volume* vol, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return RF_OK;
+  return set_error(vol, RF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+DevFrame make_dev_frame(const rf_frame* f) {
+  DevFrame d;
+  d.H = f->height;
+  d.W = f->width;
+  d.fx = (float)f->fx;
+  d.fy = (float)f->fy;
+  d.cx = (float)f->cx;
+  d.cy = (float)f->cy;
+  d.ifx = (float)(1.0 / f->fx);
+  d.ify = (float)(1.0 / f->fy);
+  d.fxd = f->fx;
+  d.fyd = f->fy;
+  d.cxd = f->cx;
+  d.cyd = f->cy;
+  d.fxq = llround(f->fx * 256.0);
+  d.fyq = llround(f->fy * 256.0);
+  d.cxq = llround((f->cx + 0.5) * 256.0);
+  d.cyq = llround((f->cy + 0.5) * 256.0);
+  d.depth = f->depth;
+  d.rgb = f->rgb;
+  return d;
+}
+
+void prof_record(rf_volume* vol, int ev, cudaStream_t st) {
+  // External records stay event-record nodes when captured into a graph.
+  if (vol->profiling) cudaEventRecordWithFlags(vol->ev[ev], st, cudaEventRecordExternal);
+}
+
+bool frame_ok(const rf_volume* vol, const rf_frame* f) {
+  if (!f || !f->depth || !f->rgb) return false;
+  if (f->height <= 0 || f->width <= 0 || f->height > vol->max_h || f->width > vol->max_w) return false;
+  if (!(f->fx > 0.0 && f->fy > 0.0 && f->fx < 4096.0 && f->fy < 4096.0)) return false;
+  if (!(std::fabs(f->cx) < 8192.0 && std::fabs(f->cy) < 8192.0)) return false;
+  return true;
+}
+
+}  // namespace rf
+
+using namespace rf;
+
+namespace {
+
+template <class T>
+rf_status dalloc(rf_volume* vol, T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return set_error(vol, RF_ERR_CUDA, "cudaMalloc(%s, %zu bytes): %s", what, count * sizeof(T),
+                                         cudaGetErrorString(e));
+  vol->device_bytes += count * sizeof(T);
+  return RF_OK;
+}
+
+bool is_integer(double x) { return std::fabs(x - std::llround(x)) < 1e-6; }
+
+rf_status validate_params(const rf_params* p) {
+  if (!(p->voxel_size > 0.0 && p->voxel_size <= 1.0) || !is_integer(p->voxel_size * 1e6))
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "voxel_size must be a positive whole number of micrometres");
+  if (!(p->trunc > 0.0 && p->trunc < 10.0)) return set_error(nullptr, RF_ERR_INVALID_ARG, "trunc out of range");
+  if (!(p->depth_scale > 0.0) || !is_integer(1e6 / p->depth_scale))
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "1e6/depth_scale must be an integer");
+  if (!(p->d_min >= 0.0 && p->d_max > p->d_min && p->d_max <= 50.0))
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "need 0 <= d_min < d_max <= 50 m");
+  if (!(p->z_near > 0.0 && p->z_near < p->d_max)) return set_error(nullptr, RF_ERR_INVALID_ARG, "z_near out of range");
+  if (p->w_max < 1 || p->w_max > 255) return set_error(nullptr, RF_ERR_INVALID_ARG, "w_max must be in 1..255");
+  if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) return set_error(nullptr, RF_ERR_INVALID_ARG, "gamma must be in [0,1]");
+  if (!(p->theta >= 0.0 && p->theta < 1.0)) return set_error(nullptr, RF_ERR_INVALID_ARG, "theta must be in [0,1)");
+  if (!(p->w_c >= 0.0)) return set_error(nullptr, RF_ERR_INVALID_ARG, "w_c must be >= 0");
+  for (int l = 0; l < 3; ++l) {
+    if (p->lm_iters[l] < 0 || p->lm_iters[l] > 1000) return set_error(nullptr, RF_ERR_INVALID_ARG, "lm_iters");
+    if (p->lm_strides[l] < 1 || p->lm_strides[l] > 64) return set_error(nullptr, RF_ERR_INVALID_ARG, "lm_strides");
+  }
+  if (p->max_ff_sweeps < 1 || p->max_ff_sweeps > (1 << 20))
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "max_ff_sweeps");
+  if (p->max_candidates < 1 || p->max_candidates > (int64_t)1 << 28)
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "max_candidates");
+  return RF_OK;
+}
+
+DevParams derive(const rf_params& p) {
+  DevParams d;
+  d.voxel = (float)p.voxel_size;
+  d.inv_voxel = (float)(1.0 / p.voxel_size);
+  d.tau = (float)p.trunc;
+  d.w_c = (float)p.w_c;
+  d.gamma_tau2 = (float)(p.gamma * p.trunc * p.trunc);
+  d.inv_depth_scale = (float)(1.0 / p.depth_scale);
+  d.z_near = (float)p.z_near;
+  d.d_max = (float)p.d_max;
+  d.voxel_d = p.voxel_size;
+  d.tau_d = p.trunc;
+  d.gamma_d = p.gamma;
+  d.depth_scale_d = p.depth_scale;
+  d.v_um = llround(p.voxel_size * 1e6);
+  d.du_um = llround(1e6 / p.depth_scale);
+  d.dmin_um = llround(p.d_min * 1e6);
+  d.dmax_um = llround(p.d_max * 1e6);
+  d.znear_tick = llround(p.z_near * 1e6) * 1024;
+  d.dmax_tick = d.dmax_um * 1024;
+  d.tau_tick = llround(p.trunc * 1e6 * 1024.0);
+  d.w_max = p.w_max;
+  d.theta_ppm = llround(p.theta * 1e6);
+  return d;
+}
+
+__global__ void k_fill_u64(unsigned long long* p, size_t n, unsigned long long v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void k_import(DevVol v, const int4* __restrict__ coords, int n, int base) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int i = base + j;
+  const int4 c = coords[j];
+  if (!coord_ok(c.x, c.y, c.z)) {
+    atomicOr(v.status, ST_OUT_OF_RANGE);
+    return;
+  }
+  const unsigned long long key = pack_key(c.x, c.y, c.z);
+  const unsigned long long b = mix64(key) & v.bucket_mask;
+  for (int pr = 0; pr < kMaxProbe; ++pr) {
+    unsigned long long* bp = v.hash + ((b + pr) & v.bucket_mask) * kSlots;
+    for (int s = 0; s < kSlots; ++s) {
+      const unsigned long long prev = atomicCAS(bp + s, kEmpty, (key << 22) | (unsigned long long)i);
+      if (prev == kEmpty) {
+        v.coords[i] = make_int4(c.x, c.y, c.z, 1);
+        return;
+      }
+      if ((prev >> 22) == key) return;  // duplicate coordinate in the snapshot: first one wins
+    }
+  }
+  atomicOr(v.status, ST_HASH_FULL);
+}
+
+rf_status clear_model(rf_volume* vol, cudaStream_t st) {
+  const size_t n = (size_t)vol->n_buckets * kSlots;
+  k_fill_u64<<<vol->sm_count * 4, 256, 0, st>>>(vol->d_hash, n, kEmpty);
+  rf_status s = check_cuda(vol, cudaGetLastError(), "hash clear");
+  if (s) return s;
+  if ((s = check_cuda(vol, cudaMemsetAsync(vol->d_nblocks, 0, sizeof(int), st), "pool reset"))) return s;
+  if ((s = check_cuda(vol, cudaMemsetAsync(vol->d_coords, 0, sizeof(int4) * vol->max_blocks, st), "coords reset")))
+    return s;
+  return RF_OK;
+}
+
+rf_status status_from_bits(rf_volume* vol, unsigned bits) {
+  if (bits == 0) return RF_OK;
+  if (bits & ST_HASH_FULL) return set_error(vol, RF_ERR_HASH_FULL, "hash table full (bounded probe exhausted)");
+  if (bits & ST_POOL_FULL) return set_error(vol, RF_ERR_POOL_FULL, "block pool full (max_blocks reached)");
+  if (bits & ST_CAPACITY) return set_error(vol, RF_ERR_CAPACITY, "frustum candidate list overflow");
+  if (bits & ST_OUT_OF_RANGE) return set_error(vol, RF_ERR_OUT_OF_RANGE, "block coordinate outside +-8191");
+  if (bits & ST_BARRIER) return set_error(vol, RF_ERR_NOT_CONVERGED, "grid barrier timed out");
+  if (bits & ST_NOT_CONVERGED) return set_error(vol, RF_ERR_NOT_CONVERGED, "flood fill exceeded max_ff_sweeps");
+  return set_error(vol, RF_ERR_CUDA, "unknown device status 0x%x", bits);
+}
+
+// Enqueues the device work of one whole frame on `st`, reading the staging
+// buffers of the volume only (so that it can be captured into a graph).
+rf_status enqueue_frame(rf_volume* vol, const DevFrame& f, bool first, cudaStream_t st) {
+  double* Tin = vol->d_T;
+  double* T1 = vol->d_T + 16;
+  double* T2 = vol->d_T + 32;
+  rf_status s;
+  prof_record(vol, EV_FRAME0, st);
+  if (first) {
+    if ((s = check_cuda(vol, cudaMemsetAsync(vol->d_mask, 0, (size_t)f.H * f.W, st), "mask clear"))) return s;
+    prof_record(vol, EV_TRACK1_END, st);
+    prof_record(vol, EV_MASK_END, st);
+    prof_record(vol, EV_TRACK2_END, st);
+    prof_record(vol, EV_INTEG0, st);
+    if ((s = launch_integrate(vol, f, Tin, nullptr, st))) return s;
+    s = check_cuda(vol, cudaMemcpyAsync(T2, Tin, 16 * sizeof(double), cudaMemcpyDeviceToDevice, st), "pose copy");
+    prof_record(vol, EV_FRAME1, st);
+    return s;
+  }
+  if ((s = launch_track(vol, f, Tin, nullptr, T1, nullptr, st))) return s;
+  prof_record(vol, EV_TRACK1_END, st);
+  if ((s = launch_mask(vol, f, T1, vol->d_mask, st))) return s;
+  prof_record(vol, EV_MASK_END, st);
+  if ((s = launch_track(vol, f, T1, vol->d_mask, T2, vol->d_info, st))) return s;
+  prof_record(vol, EV_TRACK2_END, st);
+  prof_record(vol, EV_INTEG0, st);
+  s = launch_integrate(vol, f, T2, vol->d_mask, st);
+  prof_record(vol, EV_FRAME1, st);
+  return s;
+}
+
+rf_status frame_graph(rf_volume* vol, const rf_frame* fr, bool first, cudaGraphExec_t* out) {
+  for (const auto& g : vol->graphs)
+    if (g.H == fr->height && g.W == fr->width && g.fx == fr->fx && g.fy == fr->fy && g.cx == fr->cx &&
+        g.cy == fr->cy && g.first == (int)first && g.profiling == (int)vol->profiling) {
+      *out = g.exec;
+      return RF_OK;
+    }
+  rf_frame staged = *fr;
+  staged.depth = vol->d_depth;
+  staged.rgb = vol->d_rgb;
+  const DevFrame f = make_dev_frame(&staged);
+  cudaStream_t cap;
+  rf_status s = check_cuda(vol, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+  if (s) return s;
+  s = check_cuda(vol, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (s) {
+    cudaStreamDestroy(cap);
+    return s;
+  }
+  rf_status es = enqueue_frame(vol, f, first, cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+  cudaStreamDestroy(cap);
+  if (es) {
+    if (graph) cudaGraphDestroy(graph);
+    return es;
+  }
+  if ((s = check_cuda(vol, ce, "end capture"))) return s;
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if ((s = check_cuda(vol, ce, "graph instantiate"))) return s;
+  if (vol->graphs.size() >= 16) {
+    cudaGraphExecDestroy(vol->graphs.front().exec);
+    vol->graphs.erase(vol->graphs.begin());
+  }
+  vol->graphs.push_back(
+      rf_graph_entry{fr->height, fr->width, fr->fx, fr->fy, fr->cx, fr->cy, (int)first, (int)vol->profiling, exec});
+  *out = exec;
+  return RF_OK;
+}
+
+// Replays the captured graph, or enqueues the kernels directly when graphs
+// are disabled (RF_NO_GRAPHS=1 in the environment at volume creation).
+rf_status run_frame(rf_volume* vol, const rf_frame* fr, bool first, cudaGraphExec_t exec, cudaStream_t st) {
+  if (exec) return check_cuda(vol, cudaGraphLaunch(exec, st), "graph launch");
+  rf_frame staged = *fr;
+  staged.depth = vol->d_depth;
+  staged.rgb = vol->d_rgb;
+  return enqueue_frame(vol, make_dev_frame(&staged), first, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+rf_status rf_default_params(rf_params* p) {
+  if (!p) return RF_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->voxel_size = 0.01;  // Tab. I
+  p->trunc = 0.1;        // Tab. I
+  p->w_c = 0.025;        // Tab. I
+  p->theta = 0.007;      // Tab. I
+  p->gamma = 0.5;        // Tab. I
+  p->depth_scale = 1000.0;
+  p->d_min = 0.2;
+  p->d_max = 5.0;
+  p->z_near = 0.2;
+  p->w_max = 255;
+  p->lm_iters[0] = 10;
+  p->lm_iters[1] = 5;
+  p->lm_iters[2] = 5;
+  p->lm_strides[0] = 4;
+  p->lm_strides[1] = 2;
+  p->lm_strides[2] = 1;
+  p->lm_lambda0 = 1e-4;
+  p->lm_eps_trans = 1e-6;
+  p->lm_eps_rot = 1e-6;
+  p->lm_min_valid = 10;
+  p->max_ff_sweeps = 4096;
+  p->max_candidates = (int64_t)1 << 21;
+  return RF_OK;
+}
+
+const char* rf_status_string(rf_status s) {
+  switch (s) {
+    case RF_OK: return "ok";
+    case RF_ERR_INVALID_ARG: return "invalid argument";
+    case RF_ERR_CUDA: return "CUDA error";
+    case RF_ERR_HASH_FULL: return "hash table full";
+    case RF_ERR_POOL_FULL: return "block pool full";
+    case RF_ERR_NOT_CONVERGED: return "not converged";
+    case RF_ERR_BUFFER_TOO_SMALL: return "buffer too small";
+    case RF_ERR_OUT_OF_RANGE: return "block coordinate out of range";
+    case RF_ERR_CAPACITY: return "candidate capacity exceeded";
+  }
+  return "unknown status";
+}
+
+const char* rf_last_error(rf_volume* vol) { return vol ? vol->last_error.c_str() : g_create_error.c_str(); }
+
+rf_status rf_destroy_volume(rf_volume* vol) {
+  if (!vol) return RF_OK;
+  cudaDeviceSynchronize();
+  for (auto& g : vol->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& e : vol->ev)
+    if (e) cudaEventDestroy(e);
+  void* dev[] = {vol->d_hash, vol->d_vox,  vol->d_W,       vol->d_coords, vol->d_nblocks, vol->d_status,
+                 vol->d_lm,   vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
+                 vol->d_tilemax, vol->d_cand, vol->d_depth, vol->d_rgb,   vol->d_mask,    vol->d_T, vol->d_info,
+                 vol->d_guard};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  delete vol;
+  return RF_OK;
+}
+
+rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width, int max_height,
+                           rf_volume** out) {
+  if (!out) return set_error(nullptr, RF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!p) return set_error(nullptr, RF_ERR_INVALID_ARG, "params is NULL");
+  rf_status s = validate_params(p);
+  if (s) return s;
+  if (n_buckets < 1 || (n_buckets & (n_buckets - 1)) != 0 || n_buckets > ((int64_t)1 << 30))
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "n_buckets must be a power of two <= 2^30");
+  if (max_blocks < 1 || max_blocks > kMaxPool) return set_error(nullptr, RF_ERR_INVALID_ARG, "max_blocks out of range");
+  if (max_width < 1 || max_height < 1 || max_width > 8192 || max_height > 8192)
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "frame size out of range");
+  rf_volume* vol = new rf_volume();
+  vol->p = *p;
+  vol->dp = derive(*p);
+  vol->n_buckets = n_buckets;
+  vol->max_blocks = max_blocks;
+  vol->max_w = max_width;
+  vol->max_h = max_height;
+  cudaError_t e = cudaGetDevice(&vol->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&vol->sm_count, cudaDevAttrMultiProcessorCount, vol->device);
+  if (e != cudaSuccess) {
+    s = set_error(nullptr, RF_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    delete vol;
+    return s;
+  }
+  const size_t npix = (size_t)max_width * max_height;
+  vol->max_partials = 4 * vol->sm_count;
+  const size_t ntiles = ((size_t)(max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
+  const size_t nslots = (size_t)n_buckets * kSlots;
+  if ((s = dalloc(vol, &vol->d_hash, nslots, "hash")) || (s = dalloc(vol, &vol->d_vox, (size_t)max_blocks * kBV, "voxels")) ||
+      (s = dalloc(vol, &vol->d_W, (size_t)max_blocks * kBV, "weights")) ||
+      (s = dalloc(vol, &vol->d_coords, (size_t)max_blocks, "coords")) || (s = dalloc(vol, &vol->d_nblocks, 1, "pool")) ||
+      (s = dalloc(vol, &vol->d_status, 1, "status")) || (s = dalloc(vol, &vol->d_lm, 1, "lm")) ||
+      (s = dalloc(vol, &vol->d_partials, (size_t)vol->max_partials * kPartialStride, "partials")) ||
+      (s = dalloc(vol, &vol->d_seeds, npix, "seeds")) || (s = dalloc(vol, &vol->d_md, npix, "mask work")) ||
+      (s = dalloc(vol, &vol->d_ff, (size_t)p->max_ff_sweeps + 2, "flood-fill words")) ||
+      (s = dalloc(vol, &vol->d_integ, 1, "integ")) || (s = dalloc(vol, &vol->d_tilemax, ntiles, "tiles")) ||
+      (s = dalloc(vol, &vol->d_cand, (size_t)p->max_candidates, "candidates")) ||
+      (s = dalloc(vol, &vol->d_depth, npix, "depth staging")) || (s = dalloc(vol, &vol->d_rgb, npix * 3, "rgb staging")) ||
+      (s = dalloc(vol, &vol->d_mask, npix, "mask staging")) || (s = dalloc(vol, &vol->d_T, 48, "poses")) ||
+      (s = dalloc(vol, &vol->d_info, 1, "info")) || (s = dalloc(vol, &vol->d_guard, 1, "guard count"))) {
+    g_create_error = vol->last_error;
+    rf_destroy_volume(vol);
+    return s;
+  }
+  vol->dv.hash = vol->d_hash;
+  vol->dv.bucket_mask = (unsigned long long)n_buckets - 1;
+  vol->dv.vox = vol->d_vox;
+  vol->dv.W = vol->d_W;
+  vol->dv.coords = vol->d_coords;
+  vol->dv.n_blocks = vol->d_nblocks;
+  vol->dv.max_blocks = (int)max_blocks;
+  vol->dv.status = vol->d_status;
+  {
+    const char* env = std::getenv("RF_NO_GRAPHS");
+    vol->use_graphs = !(env && env[0] == '1');
+  }
+  vol->ff_grid = floodfill_max_grid(vol->device);
+  if (vol->ff_grid < 1) vol->ff_grid = 1;
+  s = clear_model(vol, 0);
+  if (!s) s = check_cuda(vol, cudaMemset(vol->d_status, 0, sizeof(unsigned)), "status reset");
+  if (!s) s = check_cuda(vol, cudaDeviceSynchronize(), "create sync");
+  if (s) {
+    g_create_error = vol->last_error;
+    rf_destroy_volume(vol);
+    return s;
+  }
+  *out = vol;
+  return RF_OK;
+}
+
+rf_status rf_volume_reset(rf_volume* vol) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  rf_status s = clear_model(vol, 0);
+  if (!s) s = check_cuda(vol, cudaMemset(vol->d_status, 0, sizeof(unsigned)), "status reset");
+  if (!s) s = check_cuda(vol, cudaDeviceSynchronize(), "reset sync");
+  vol->frames = 0;
+  return s;
+}
+
+rf_status rf_track_frame(rf_volume* vol, const rf_frame* frame, const double* T_init_dev, const uint8_t* mask_dev,
+                         double* T_out_dev, rf_track_info* info_dev, void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (!frame_ok(vol, frame)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
+  if (!T_init_dev || !T_out_dev) return set_error(vol, RF_ERR_INVALID_ARG, "pose pointer is NULL");
+  return launch_track(vol, make_dev_frame(frame), T_init_dev, mask_dev, T_out_dev, info_dev, (cudaStream_t)stream);
+}
+
+rf_status rf_compute_mask(rf_volume* vol, const rf_frame* frame, const double* T_dev, uint8_t* mask_dev, void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (!frame_ok(vol, frame)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
+  if (!T_dev || !mask_dev) return set_error(vol, RF_ERR_INVALID_ARG, "NULL pose or mask");
+  return launch_mask(vol, make_dev_frame(frame), T_dev, mask_dev, (cudaStream_t)stream);
+}
+
+rf_status rf_integrate_frame(rf_volume* vol, const rf_frame* frame, const double* T_dev, const uint8_t* mask_dev,
+                             void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (!frame_ok(vol, frame)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
+  if (!T_dev) return set_error(vol, RF_ERR_INVALID_ARG, "NULL pose");
+  return launch_integrate(vol, make_dev_frame(frame), T_dev, mask_dev, (cudaStream_t)stream);
+}
+
+rf_status rf_process_frame(rf_volume* vol, const rf_frame* frame, const double* T_init_dev, double* T_out_dev,
+                           uint8_t* mask_dev, rf_track_info* info_dev, void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (!frame_ok(vol, frame)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
+  if (!T_init_dev || !T_out_dev) return set_error(vol, RF_ERR_INVALID_ARG, "NULL pose");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t npix = (size_t)frame->height * frame->width;
+  const bool first = vol->frames == 0;
+  cudaGraphExec_t exec = nullptr;
+  rf_status s = vol->use_graphs ? frame_graph(vol, frame, first, &exec) : RF_OK;
+  if (s) return s;
+  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_depth, frame->depth, npix * 2, cudaMemcpyDeviceToDevice, st),
+                      "depth staging")))
+    return s;
+  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_rgb, frame->rgb, npix * 3, cudaMemcpyDeviceToDevice, st),
+                      "rgb staging")))
+    return s;
+  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_T, T_init_dev, 16 * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                      "pose staging")))
+    return s;
+  if ((s = run_frame(vol, frame, first, exec, st))) return s;
+  if ((s = check_cuda(vol, cudaMemcpyAsync(T_out_dev, vol->d_T + 32, 16 * sizeof(double), cudaMemcpyDeviceToDevice, st),
+                      "pose out")))
+    return s;
+  if (mask_dev && (s = check_cuda(vol, cudaMemcpyAsync(mask_dev, vol->d_mask, npix, cudaMemcpyDeviceToDevice, st),
+                                  "mask out")))
+    return s;
+  if (info_dev) {
+    if (first) s = check_cuda(vol, cudaMemsetAsync(info_dev, 0, sizeof(rf_track_info), st), "info out");
+    else s = check_cuda(vol, cudaMemcpyAsync(info_dev, vol->d_info, sizeof(rf_track_info), cudaMemcpyDeviceToDevice, st),
+                        "info out");
+    if (s) return s;
+  }
+  vol->frames++;
+  return RF_OK;
+}
+
+rf_status rf_process_frame_host(rf_volume* vol, int height, int width, const double intrinsics[4],
+                                const uint16_t* depth_host, const uint8_t* rgb_host, const double T_init_host[16],
+                                double T_out_host[16], uint8_t* mask_host, void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (!intrinsics || !depth_host || !rgb_host || !T_init_host || !T_out_host)
+    return set_error(vol, RF_ERR_INVALID_ARG, "NULL host buffer");
+  rf_frame fr{height, width, intrinsics[0], intrinsics[1], intrinsics[2], intrinsics[3], vol->d_depth, vol->d_rgb};
+  if (!frame_ok(vol, &fr)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t npix = (size_t)height * width;
+  const bool first = vol->frames == 0;
+  cudaGraphExec_t exec = nullptr;
+  rf_status s = vol->use_graphs ? frame_graph(vol, &fr, first, &exec) : RF_OK;
+  if (s) return s;
+  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_depth, depth_host, npix * 2, cudaMemcpyHostToDevice, st), "depth H2D")) ||
+      (s = check_cuda(vol, cudaMemcpyAsync(vol->d_rgb, rgb_host, npix * 3, cudaMemcpyHostToDevice, st), "rgb H2D")) ||
+      (s = check_cuda(vol, cudaMemcpyAsync(vol->d_T, T_init_host, 16 * sizeof(double), cudaMemcpyHostToDevice, st),
+                      "pose H2D")) ||
+      (s = run_frame(vol, &fr, first, exec, st)) ||
+      (s = check_cuda(vol, cudaMemcpyAsync(T_out_host, vol->d_T + 32, 16 * sizeof(double), cudaMemcpyDeviceToHost, st),
+                      "pose D2H")))
+    return s;
+  if (mask_host && (s = check_cuda(vol, cudaMemcpyAsync(mask_host, vol->d_mask, npix, cudaMemcpyDeviceToHost, st),
+                                   "mask D2H")))
+    return s;
+  vol->frames++;
+  return rf_sync_status(vol, stream);
+}
+
+rf_status rf_extract_mesh(rf_volume* vol, float* verts_dev, uint8_t* colors_dev, int64_t cap_tris, int64_t* n_tris_host,
+                          void* stream) {
+  if (!vol || !n_tris_host) return RF_ERR_INVALID_ARG;
+  if ((verts_dev == nullptr) != (colors_dev == nullptr))
+    return set_error(vol, RF_ERR_INVALID_ARG, "verts and colors must both be given or both be NULL");
+  if (verts_dev && cap_tris < 0) return set_error(vol, RF_ERR_INVALID_ARG, "negative capacity");
+  return run_mesh(vol, verts_dev, colors_dev, cap_tris, n_tris_host, (cudaStream_t)stream);
+}
+
+rf_status rf_volume_export(rf_volume* vol, int64_t cap_blocks, int32_t* coords, float* F, uint8_t* W, uint8_t* rgb,
+                           uint8_t* wc, int64_t* n_blocks) {
+  if (!vol || !n_blocks) return RF_ERR_INVALID_ARG;
+  rf_status s = check_cuda(vol, cudaDeviceSynchronize(), "export sync");
+  if (s) return s;
+  int nb = 0;
+  if ((s = check_cuda(vol, cudaMemcpy(&nb, vol->d_nblocks, sizeof(int), cudaMemcpyDeviceToHost), "export count")))
+    return s;
+  nb = std::min<int64_t>(nb, vol->max_blocks);
+  std::vector<int4> c(nb > 0 ? nb : 1);
+  if (nb > 0 && (s = check_cuda(vol, cudaMemcpy(c.data(), vol->d_coords, sizeof(int4) * nb, cudaMemcpyDeviceToHost),
+                                "export coords")))
+    return s;
+  std::vector<int> order;
+  for (int i = 0; i < nb; ++i)
+    if (c[i].w) order.push_back(i);
+  *n_blocks = (int64_t)order.size();
+  if (!coords) return RF_OK;
+  if (!F || !W || !rgb || !wc) return set_error(vol, RF_ERR_INVALID_ARG, "export buffers must all be given");
+  if ((int64_t)order.size() > cap_blocks)
+    return set_error(vol, RF_ERR_BUFFER_TOO_SMALL, "volume has %zu blocks, buffer holds %lld", order.size(),
+                     (long long)cap_blocks);
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (c[a].z != c[b].z) return c[a].z < c[b].z;
+    if (c[a].y != c[b].y) return c[a].y < c[b].y;
+    return c[a].x < c[b].x;
+  });
+  std::vector<uint2> vx(kBV);
+  std::vector<uint8_t> w(kBV);
+  for (size_t n = 0; n < order.size(); ++n) {
+    const int pool = order[n];
+    if ((s = check_cuda(vol, cudaMemcpy(vx.data(), vol->d_vox + (size_t)pool * kBV, sizeof(uint2) * kBV,
+                                        cudaMemcpyDeviceToHost), "export voxels")) ||
+        (s = check_cuda(vol, cudaMemcpy(w.data(), vol->d_W + (size_t)pool * kBV, kBV, cudaMemcpyDeviceToHost),
+                        "export weights")))
+      return s;
+    coords[n * 3 + 0] = c[pool].x;
+    coords[n * 3 + 1] = c[pool].y;
+    coords[n * 3 + 2] = c[pool].z;
+    for (int i = 0; i < kBV; ++i) {
+      float f;
+      std::memcpy(&f, &vx[i].x, 4);
+      F[n * kBV + i] = w[i] ? f : 0.0f;
+      W[n * kBV + i] = w[i];
+      rgb[(n * kBV + i) * 3 + 0] = (uint8_t)(vx[i].y & 255u);
+      rgb[(n * kBV + i) * 3 + 1] = (uint8_t)((vx[i].y >> 8) & 255u);
+      rgb[(n * kBV + i) * 3 + 2] = (uint8_t)((vx[i].y >> 16) & 255u);
+      wc[n * kBV + i] = (uint8_t)(vx[i].y >> 24);
+    }
+  }
+  return RF_OK;
+}
+
+rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coords, const float* F, const uint8_t* W,
+                           const uint8_t* rgb, const uint8_t* wc) {
+  if (!vol || n_blocks < 0) return RF_ERR_INVALID_ARG;
+  if (n_blocks > 0 && (!coords || !F || !W || !rgb || !wc)) return set_error(vol, RF_ERR_INVALID_ARG, "NULL buffer");
+  if (n_blocks > vol->max_blocks) return set_error(vol, RF_ERR_POOL_FULL, "snapshot larger than max_blocks");
+  rf_status s = rf_volume_reset(vol);
+  if (s) return s;
+  if (n_blocks == 0) return RF_OK;
+  std::vector<uint2> vx((size_t)n_blocks * kBV);
+  std::vector<int4> c(n_blocks);
+  for (int64_t n = 0; n < n_blocks; ++n) {
+    c[n] = make_int4(coords[n * 3], coords[n * 3 + 1], coords[n * 3 + 2], 0);
+    for (int i = 0; i < kBV; ++i) {
+      const size_t k = (size_t)n * kBV + i;
+      float f = W[k] ? F[k] : std::nanf("");
+      unsigned bits;
+      std::memcpy(&bits, &f, 4);
+      if (W[k] == 0) bits = 0x7fc00000u;
+      vx[k] = make_uint2(bits, (unsigned)rgb[k * 3] | ((unsigned)rgb[k * 3 + 1] << 8) | ((unsigned)rgb[k * 3 + 2] << 16) |
+                                   ((unsigned)wc[k] << 24));
+    }
+  }
+  s = check_cuda(vol, cudaMemcpy(vol->d_vox, vx.data(), sizeof(uint2) * vx.size(), cudaMemcpyHostToDevice),
+                 "import voxels");
+  if (!s) s = check_cuda(vol, cudaMemcpy(vol->d_W, W, (size_t)n_blocks * kBV, cudaMemcpyHostToDevice), "import weights");
+  // block coordinates go through the candidate buffer (no allocation), in chunks
+  const int64_t chunk = vol->p.max_candidates;
+  for (int64_t base = 0; !s && base < n_blocks; base += chunk) {
+    const int n = (int)std::min<int64_t>(chunk, n_blocks - base);
+    s = check_cuda(vol, cudaMemcpy(vol->d_cand, c.data() + base, sizeof(int4) * n, cudaMemcpyHostToDevice),
+                   "import coords");
+    if (!s) {
+      k_import<<<(n + 255) / 256, 256>>>(vol->dv, vol->d_cand, n, (int)base);
+      s = check_cuda(vol, cudaGetLastError(), "import launch");
+    }
+    if (!s) s = check_cuda(vol, cudaDeviceSynchronize(), "import sync");
+  }
+  int nb = (int)n_blocks;
+  if (!s) s = check_cuda(vol, cudaMemcpy(vol->d_nblocks, &nb, sizeof(int), cudaMemcpyHostToDevice), "import count");
+  if (s) return s;
+  return rf_sync_status(vol, nullptr);
+}
+
+rf_status rf_volume_stats(rf_volume* vol, rf_stats* out) {
+  if (!vol || !out) return RF_ERR_INVALID_ARG;
+  int nb = 0;
+  rf_status s = check_cuda(vol, cudaMemcpy(&nb, vol->d_nblocks, sizeof(int), cudaMemcpyDeviceToHost), "stats");
+  if (s) return s;
+  out->n_blocks = std::min<int64_t>(nb, vol->max_blocks);
+  out->max_blocks = vol->max_blocks;
+  out->n_buckets = vol->n_buckets;
+  out->frames = vol->frames;
+  out->load_factor = (double)out->n_blocks / (double)(vol->n_buckets * kSlots);
+  out->device_bytes = (int64_t)vol->device_bytes;
+  return RF_OK;
+}
+
+rf_status rf_set_profiling(rf_volume* vol, int enable) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (enable && !vol->ev[0]) {
+    for (auto& e : vol->ev) {
+      rf_status s = check_cuda(vol, cudaEventCreate(&e), "event create");
+      if (s) return s;
+    }
+  }
+  vol->profiling = enable != 0;
+  return RF_OK;
+}
+
+rf_status rf_get_profile(rf_volume* vol, void* stream, rf_profile* out) {
+  if (!vol || !out) return RF_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  rf_status s = check_cuda(vol, cudaStreamSynchronize((cudaStream_t)stream), "profile sync");
+  if (s) return s;
+  if (vol->profiling) {
+    auto ms = [&](int a, int b) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, vol->ev[a], vol->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        t = -1.0f;
+      }
+      return t;
+    };
+    out->frame_ms = ms(EV_FRAME0, EV_FRAME1);
+    out->track_ms[0] = ms(EV_FRAME0, EV_TRACK1_END);
+    out->mask_ms = ms(EV_TRACK1_END, EV_MASK_END);
+    out->track_ms[1] = ms(EV_MASK_END, EV_TRACK2_END);
+    out->integrate_ms = ms(EV_INTEG0, EV_FRAME1);
+    out->integrate_kernel_ms = ms(EV_KERNEL0, EV_KERNEL1);
+  }
+  IntegState is;
+  unsigned guard = 0;
+  if ((s = check_cuda(vol, cudaMemcpy(&is, vol->d_integ, sizeof(is), cudaMemcpyDeviceToHost), "profile counters")) ||
+      (s = check_cuda(vol, cudaMemcpy(&guard, vol->d_guard, sizeof(guard), cudaMemcpyDeviceToHost), "guard count")))
+    return s;
+  out->candidates = std::min<int64_t>(is.n_cand, vol->p.max_candidates);
+  out->updated_voxels = (int64_t)is.updated;
+  out->new_blocks = is.new_blocks;
+  out->guard_pixels = guard;
+  return RF_OK;
+}
+
+rf_status rf_sync_status(rf_volume* vol, void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  rf_status s = check_cuda(vol, cudaStreamSynchronize(st), "stream sync");
+  if (s) return s;
+  unsigned bits = 0;
+  if ((s = check_cuda(vol, cudaMemcpy(&bits, vol->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost), "status read")))
+    return s;
+  if (bits && (s = check_cuda(vol, cudaMemset(vol->d_status, 0, sizeof(unsigned)), "status clear"))) return s;
+  return status_from_bits(vol, bits);
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+// Internal device structures of the ReFusion CUDA library (sm_103a).
+//
+// Model (ReFusion Sec. III-A): a TSDF on a voxel lattice, voxel k at world
+// position voxel_size * k, stored sparsely in 8x8x8 blocks addressed through a
+// spatial hash.  Per voxel:
+//   vox[i].x : SDF value F as float bits; NaN marks a never-observed voxel
+//              (this is exactly W == 0, so lookups need not read W)
+//   vox[i].y : R | G << 8 | B << 16 | Wc << 24   (RGB8 colour, colour weight)
+//   W[i]     : SDF weight (uint8, capped at w_max)
+// Block b owns vox[b*512 .. b*512+511], voxel (x,y,z) at index x + 8y + 64z.
+//
+// Hash: n_buckets buckets of 4 slots; a slot holds one 64-bit word
+//   key(42 bits: 14-bit two's complement bx, by, bz) << 22 | pool index (22 bits)
+// or ~0 when empty.  Linear probing over buckets, at most kMaxProbe buckets.
+// Entries are never deleted, so the first empty slot ends a search, and one
+// 64-bit CAS publishes key and value together.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "refusion.h"
+
+namespace rf {
+
+constexpr int kBV = 512;  // voxels per block
+constexpr int kSlots = 4;
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kMaxProbe = 64;
+constexpr int kMaxCoord = 8191;  // |block coordinate| bound of the 14-bit key fields
+constexpr int kMaxPool = (1 << 22) - 2;
+constexpr int kPartialStride = 32;  // floats per CTA partial of the normal equations
+constexpr int kTile = 16;           // depth-max tiles used by the frustum cull
+
+// device status bits (OR-ed by kernels, read by rf_sync_status)
+enum : unsigned {
+  ST_HASH_FULL = 1u,
+  ST_POOL_FULL = 2u,
+  ST_NOT_CONVERGED = 4u,
+  ST_OUT_OF_RANGE = 8u,
+  ST_CAPACITY = 16u,
+  ST_BARRIER = 32u,
+};
+
+struct DevVol {
+  unsigned long long* hash;  // n_buckets * kSlots
+  unsigned long long bucket_mask;
+  uint2* vox;
+  uint8_t* W;
+  int4* coords;  // block coordinate per pool index
+  int* n_blocks;
+  int max_blocks;
+  unsigned* status;
+};
+
+// Per-volume constants derived from rf_params.
+struct DevParams {
+  float voxel, inv_voxel, tau, w_c, gamma_tau2;
+  float inv_depth_scale, z_near, d_max;
+  double voxel_d, tau_d, gamma_d, depth_scale_d;
+  long long v_um, du_um, dmin_um, dmax_um, znear_tick, dmax_tick, tau_tick;
+  int w_max;
+  long long theta_ppm;
+};
+
+// One frame in device memory plus its intrinsics in the three forms used:
+// float (tracking), double (exact mask seeds) and quantised integers
+// (integration: f*256 and (c+1/2)*256).
+struct DevFrame {
+  int H, W;
+  float fx, fy, cx, cy, ifx, ify;
+  double fxd, fyd, cxd, cyd;
+  long long fxq, fyq, cxq, cyq;
+  const uint16_t* depth;
+  const uint8_t* rgb;
+};
+
+// Levenberg-Marquardt state of one registration, resident on the device.
+struct LMState {
+  double T[16];   // accepted pose
+  double Tc[16];  // candidate pose under evaluation
+  float Rf[12];   // float copy of T   (R row-major 3x3, then t)
+  float Rcf[12];  // float copy of Tc
+  double H[21], g[6], E;
+  long long N;
+  double lambda;
+  int done;
+  rf_track_info info;
+};
+
+// Quantised pose and the frustum search region of one integration.
+struct IntegState {
+  long long A[9];  // llround(R^T * 2^30), world -> camera
+  long long tq[3]; // llround(t * 1e6), camera centre in micrometres
+  float R[9], t[3];
+  int bmin[3];
+  int dims[3];
+  long long total;
+  float zfar;
+  int clipped;
+  int max_um;
+  int n_cand;
+  int work;
+  int new_blocks;
+  unsigned long long updated;
+};
+
+__device__ __forceinline__ bool coord_ok(int bx, int by, int bz) {
+  return bx >= -kMaxCoord && bx <= kMaxCoord && by >= -kMaxCoord && by <= kMaxCoord && bz >= -kMaxCoord &&
+         bz <= kMaxCoord;
+}
+
+__device__ __forceinline__ unsigned long long pack_key(int bx, int by, int bz) {
+  return ((unsigned long long)(bx & 0x3FFF) << 28) | ((unsigned long long)(by & 0x3FFF) << 14) |
+         (unsigned long long)(bz & 0x3FFF);
+}
+
+// splitmix64 finaliser as the bucket hash
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z ^= z >> 30;
+  z *= 0xbf58476d1ce4e5b9ull;
+  z ^= z >> 27;
+  z *= 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return z;
+}
+
+// Read-only lookup for kernels that do not insert (tracking, mask, mesh).
+__device__ __forceinline__ int hash_find(const DevVol& v, int bx, int by, int bz) {
+  if (!coord_ok(bx, by, bz)) return -1;
+  const unsigned long long key = pack_key(bx, by, bz);
+  unsigned long long b = mix64(key) & v.bucket_mask;
+  for (int p = 0; p < kMaxProbe; ++p) {
+    const ulonglong2* bp = reinterpret_cast<const ulonglong2*>(v.hash + ((b + p) & v.bucket_mask) * kSlots);
+    const ulonglong2 e01 = __ldg(bp);
+    const ulonglong2 e23 = __ldg(bp + 1);
+    const unsigned long long e[4] = {e01.x, e01.y, e23.x, e23.y};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (e[s] == kEmpty) return -1;
+      if ((e[s] >> 22) == key) return (int)(e[s] & 0x3FFFFF);
+    }
+  }
+  return -1;
+}
+
+__device__ __forceinline__ float rgb_intensity(unsigned c) {
+  // Sec. III-B: I = 0.2126 R + 0.7152 G + 0.0722 B, scaled to [0, 1]
+  return (0.2126f * (float)(c & 255u) + 0.7152f * (float)((c >> 8) & 255u) + 0.0722f * (float)((c >> 16) & 255u)) *
+         (1.0f / 255.0f);
+}
+
+__device__ __forceinline__ bool pixel_valid(const DevParams& p, unsigned raw) {
+  const long long D = (long long)raw * p.du_um;
+  return raw != 0 && D >= p.dmin_um && D <= p.dmax_um;
+}
+
+// Grid-wide barrier for cooperative launches (all CTAs co-resident).  The
+// spin is bounded: after ~1 s it records ST_BARRIER and returns false, and
+// callers then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned ticket = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (ticket == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > (1ll << 24)) {
+          ok = 0;
+          atomicOr(status, ST_BARRIER);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+}  // namespace rf
+
+// Host-side helpers shared by the translation units.
+struct rf_volume;
+namespace rf {
+DevFrame make_dev_frame(const rf_frame* f);
+bool frame_ok(const rf_volume* vol, const rf_frame* f);
+rf_status set_error(rf_volume* vol, rf_status s, const char* fmt, ...);
+rf_status check_cuda(rf_volume* vol, cudaError_t e, const char* what);
+// stage launchers (stream-ordered, no host synchronisation)
+rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
+                       rf_track_info* info, cudaStream_t st);
+rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_t* mask_out, cudaStream_t st);
+rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st);
+// profiling events (no-ops unless profiling is enabled); ids below
+enum ProfEvent { EV_FRAME0, EV_TRACK1_END, EV_MASK_END, EV_TRACK2_END, EV_INTEG0, EV_KERNEL0, EV_KERNEL1, EV_FRAME1,
+                 EV_COUNT };
+void prof_record(rf_volume* vol, int ev, cudaStream_t st);
+rf_status run_mesh(rf_volume* vol, float* verts, uint8_t* colors, int64_t cap, int64_t* n, cudaStream_t st);
+}  // namespace rf

@@ -1,0 +1,277 @@
+// Dynamics detection (ReFusion Sec. III-C) on sm_103a.
+//
+//   k_seeds      r_i = V_SDF(T x_i)^2 (the residual of Eq. 2, V_SDF truncated to
+//                [-tau, tau]) and the raw mask r_i > t = gamma tau^2 (Eq. 5), one
+//                thread per pixel.  The
+//                decision is exact: the FP32 evaluation carries an error bound;
+//                when the lattice cell or the comparison is within it, the pixel
+//                is re-evaluated in FP64 with a fixed operation order and no
+//                contraction (__d*_rn), the order the FP64 oracle uses.
+//   k_erode      M_R = 3x3 erosion of the raw mask (outside the image = 0), and
+//                M_D initialised to M_R.
+//   k_floodfill  Alg. 1 closure: n joins from p when |D(p) - D(n)| < theta D(p)
+//                (4-neighbours, raw integer depth, theta in ppm).  The closure
+//                is the set reachable from M_R, independent of visiting order,
+//                so tiles propagate locally in shared memory until stable and
+//                sweep globally (cooperative launch, bounded grid barrier) until
+//                no tile changes; at most max_ff_sweeps sweeps.
+//   k_dilate     final mask = 3x3 dilation of M_D.
+#include <cmath>
+
+#include "rf_volume.hpp"
+
+namespace rf {
+namespace {
+
+__device__ __forceinline__ double lerp_rn(double a, double b, double t) {
+  const double om = __dsub_rn(1.0, t);
+  return __dadd_rn(__dmul_rn(a, om), __dmul_rn(b, t));
+}
+
+// Fetches the 8 corner SDF values of the cell with lattice origin k; false if
+// any corner is missing or unobserved.
+__device__ __forceinline__ bool corners_of(const DevVol& v, int kx, int ky, int kz, float F[8]) {
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int x = kx + (n & 1), y = ky + ((n >> 1) & 1), z = kz + ((n >> 2) & 1);
+    const int pool = hash_find(v, x >> 3, y >> 3, z >> 3);
+    if (pool < 0) return false;
+    F[n] = __uint_as_float(__ldg(&v.vox[(size_t)pool * kBV + (x & 7) + 8 * (y & 7) + 64 * (z & 7)].x));
+    if (F[n] != F[n]) return false;
+  }
+  return true;
+}
+
+// FP64 residual in the fixed evaluation order; r < 0 when the lookup is invalid.
+__device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevParams& p, const double* T, int u, int vv,
+                                unsigned raw) {
+  const double D = __ddiv_rn((double)raw, p.depth_scale_d);
+  const double x = __dmul_rn(__ddiv_rn(__dsub_rn((double)u, f.cxd), f.fxd), D);
+  const double y = __dmul_rn(__ddiv_rn(__dsub_rn((double)vv, f.cyd), f.fyd), D);
+  const double z = D;
+  double q[3];
+  int k[3];
+  double fr[3];
+  for (int i = 0; i < 3; ++i) {
+    const double pi = __dadd_rn(
+        __dadd_rn(__dadd_rn(__dmul_rn(T[i * 4 + 0], x), __dmul_rn(T[i * 4 + 1], y)), __dmul_rn(T[i * 4 + 2], z)),
+        T[i * 4 + 3]);
+    q[i] = __ddiv_rn(pi, p.voxel_d);
+    if (!(fabs(q[i]) < 1e9)) return -1.0;
+    const double fl = floor(q[i]);
+    k[i] = (int)fl;
+    fr[i] = __dsub_rn(q[i], fl);
+  }
+  if (abs(k[0]) > 8 * kMaxCoord || abs(k[1]) > 8 * kMaxCoord || abs(k[2]) > 8 * kMaxCoord) return -1.0;
+  float F[8];
+  if (!corners_of(v, k[0], k[1], k[2], F)) return -1.0;
+  const double c00 = lerp_rn(F[0], F[1], fr[0]), c10 = lerp_rn(F[2], F[3], fr[0]);
+  const double c01 = lerp_rn(F[4], F[5], fr[0]), c11 = lerp_rn(F[6], F[7], fr[0]);
+  const double c0 = lerp_rn(c00, c10, fr[1]), c1 = lerp_rn(c01, c11, fr[1]);
+  const double V = fmin(fmax(lerp_rn(c0, c1, fr[2]), -p.tau_d), p.tau_d);  // truncated at tau
+  return __dmul_rn(V, V);
+}
+
+__global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p, const double* __restrict__ T,
+                                               uint8_t* __restrict__ seeds, unsigned* guard_count) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= f.H * f.W) return;
+  const int u = idx % f.W, vv = idx / f.W;
+  const unsigned raw = __ldg(f.depth + idx);
+  uint8_t seed = 0;
+  if (pixel_valid(p, raw)) {
+    const double t64 = __dmul_rn(__dmul_rn(p.gamma_d, p.tau_d), p.tau_d);
+    const float t = (float)t64;
+    float Rf[12];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Rf[i * 3 + j] = (float)T[i * 4 + j];
+      Rf[9 + i] = (float)T[i * 4 + 3];
+    }
+    const float D = (float)raw * p.inv_depth_scale;
+    const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
+    float q[3], fr[3];
+    int k[3];
+    bool ambiguous = false;
+    const float mag_in = (fabsf(x) + fabsf(y) + fabsf(D) + fabsf(Rf[9]) + fabsf(Rf[10]) + fabsf(Rf[11])) * p.inv_voxel;
+    float qmax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float pi = Rf[i * 3] * x + Rf[i * 3 + 1] * y + Rf[i * 3 + 2] * D + Rf[9 + i];
+      q[i] = pi * p.inv_voxel;
+      qmax = fmaxf(qmax, fabsf(q[i]));
+    }
+    // bound on |q32 - q64| with an 8x margin (see the error budget in the design notes)
+    const float eps_q = (mag_in + qmax) * 3.814697265625e-06f;  // 2^-18
+    if (!(qmax < 8.0f * kMaxCoord - 2.0f)) ambiguous = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float fl = floorf(q[i]);
+      k[i] = (int)fl;
+      fr[i] = q[i] - fl;
+      if (fr[i] < eps_q || fr[i] > 1.0f - eps_q) ambiguous = true;
+    }
+    if (!ambiguous) {
+      float F[8];
+      if (corners_of(v, k[0], k[1], k[2], F)) {
+        const float c00 = F[0] * (1.0f - fr[0]) + F[1] * fr[0], c10 = F[2] * (1.0f - fr[0]) + F[3] * fr[0];
+        const float c01 = F[4] * (1.0f - fr[0]) + F[5] * fr[0], c11 = F[6] * (1.0f - fr[0]) + F[7] * fr[0];
+        const float c0 = c00 * (1.0f - fr[1]) + c10 * fr[1], c1 = c01 * (1.0f - fr[1]) + c11 * fr[1];
+        const float V = fminf(fmaxf(c0 * (1.0f - fr[2]) + c1 * fr[2], -p.tau), p.tau);
+        float fmn = F[0], fmx = F[0], fab = fabsf(F[0]);
+#pragma unroll
+        for (int n = 1; n < 8; ++n) {
+          fmn = fminf(fmn, F[n]);
+          fmx = fmaxf(fmx, F[n]);
+          fab = fmaxf(fab, fabsf(F[n]));
+        }
+        // + the gap between the float and double truncation bounds (<= 2^-24 tau)
+        const float dV = 3.0f * (fmx - fmn) * eps_q + fab * 1.9073486328125e-06f + p.tau * 5.9604645e-08f;
+        const float r = V * V;
+        const float dr = 2.0f * fabsf(V) * dV + dV * dV + r * 2.384185791015625e-07f;  // 2^-22
+        if (fabsf(r - t) <= 2.0f * dr + t * 2.384185791015625e-07f) ambiguous = true;
+        else seed = r > t ? 1 : 0;
+      }
+      // an unambiguous cell with a missing corner is invalid in FP64 too: no seed
+    }
+    if (ambiguous) {
+      const double r64 = residual_fp64(v, f, p, T, u, vv, raw);
+      seed = (r64 >= 0.0 && r64 > t64) ? 1 : 0;
+      if (guard_count) atomicAdd(guard_count, 1u);
+    }
+  }
+  seeds[idx] = seed;
+}
+
+__global__ void __launch_bounds__(256) k_erode(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ mr) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= H * W) return;
+  const int u = idx % W, v = idx / W;
+  uint8_t all = 1;
+  if (u == 0 || v == 0 || u == W - 1 || v == H - 1) {
+    all = 0;
+  } else {
+#pragma unroll
+    for (int dv = -1; dv <= 1; ++dv)
+#pragma unroll
+      for (int du = -1; du <= 1; ++du) all &= (__ldg(in + (v + dv) * W + (u + du)) != 0);
+  }
+  mr[idx] = all;
+}
+
+__global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= H * W) return;
+  const int u = idx % W, v = idx / W;
+  uint8_t any = 0;
+  for (int dv = -1; dv <= 1; ++dv) {
+    const int y = v + dv;
+    if (y < 0 || y >= H) continue;
+    for (int du = -1; du <= 1; ++du) {
+      const int x = u + du;
+      if (x < 0 || x >= W) continue;
+      any |= (__ldg(in + y * W + x) != 0);
+    }
+  }
+  out[idx] = any;
+}
+
+constexpr int kFFW = 32, kFFH = 16;  // flood-fill tile (one thread per pixel)
+constexpr int kFFThreads = kFFW * kFFH;
+
+__device__ __forceinline__ bool ff_edge(unsigned Dsrc, unsigned Ddst, long long theta_ppm) {
+  const long long diff = Dsrc > Ddst ? (long long)(Dsrc - Ddst) : (long long)(Ddst - Dsrc);
+  return diff * 1000000ll < theta_ppm * (long long)Dsrc;
+}
+
+// ff words: [0] barrier count, [1] barrier generation, [2 + s] changed in sweep s
+__global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uint16_t* __restrict__ depth, int H,
+                                                           int W, long long theta_ppm, unsigned* ff, int max_sweeps,
+                                                           unsigned* status) {
+  __shared__ uint8_t sm[kFFH + 2][kFFW + 2];
+  __shared__ uint16_t sd[kFFH + 2][kFFW + 2];
+  const int tiles_x = (W + kFFW - 1) / kFFW, tiles_y = (H + kFFH - 1) / kFFH;
+  const int ntiles = tiles_x * tiles_y;
+  const int tx = threadIdx.x % kFFW, ty = threadIdx.x / kFFW;
+  unsigned* bar = ff;
+  unsigned* changed = ff + 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int u0 = (tile % tiles_x) * kFFW, v0 = (tile / tiles_x) * kFFH;
+      // tile + 1-pixel halo into shared memory
+      for (int i = threadIdx.x; i < (kFFH + 2) * (kFFW + 2); i += kFFThreads) {
+        const int hy = i / (kFFW + 2), hx = i % (kFFW + 2);
+        const int u = u0 + hx - 1, v = v0 + hy - 1;
+        const bool in = u >= 0 && u < W && v >= 0 && v < H;
+        sm[hy][hx] = in ? *(volatile uint8_t*)(md + v * W + u) : 0;
+        sd[hy][hx] = in ? __ldg(depth + v * W + u) : 0;
+      }
+      __syncthreads();
+      const int u = u0 + tx, v = v0 + ty;
+      const bool inside = u < W && v < H;
+      bool grew = false;
+      for (int it = 0; it < kFFThreads; ++it) {
+        int c = 0;
+        if (inside && !sm[ty + 1][tx + 1]) {
+          const unsigned Dp = sd[ty + 1][tx + 1];
+          if ((sm[ty + 1][tx] && ff_edge(sd[ty + 1][tx], Dp, theta_ppm)) ||
+              (sm[ty + 1][tx + 2] && ff_edge(sd[ty + 1][tx + 2], Dp, theta_ppm)) ||
+              (sm[ty][tx + 1] && ff_edge(sd[ty][tx + 1], Dp, theta_ppm)) ||
+              (sm[ty + 2][tx + 1] && ff_edge(sd[ty + 2][tx + 1], Dp, theta_ppm))) {
+            sm[ty + 1][tx + 1] = 1;
+            grew = true;
+            c = 1;
+          }
+        }
+        if (!__syncthreads_or(c)) break;
+      }
+      if (grew) md[v * W + u] = 1;
+      if (__syncthreads_or(grew) && threadIdx.x == 0) atomicExch(changed + sweep, 1u);
+    }
+    if (!grid_barrier(bar, gridDim.x, status)) return;
+    if (*(volatile unsigned*)(changed + sweep) == 0u) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_NOT_CONVERGED);
+}
+
+}  // namespace
+
+rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_t* mask_out, cudaStream_t st) {
+  const int n = f.H * f.W;
+  const int blocks = (n + 255) / 256;
+  rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_guard, 0, sizeof(unsigned), st), "guard reset");
+  if (s != RF_OK) return s;
+  k_seeds<<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds, vol->d_guard);
+  k_erode<<<blocks, 256, 0, st>>>(vol->d_seeds, f.H, f.W, vol->d_md);
+  s = check_cuda(vol, cudaMemsetAsync(vol->d_ff, 0, sizeof(unsigned) * (2 + vol->p.max_ff_sweeps), st),
+                 "flood-fill reset");
+  if (s != RF_OK) return s;
+  const int ntiles = ((f.W + kFFW - 1) / kFFW) * ((f.H + kFFH - 1) / kFFH);
+  const int grid = ntiles < vol->ff_grid ? ntiles : vol->ff_grid;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kFFThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  s = check_cuda(vol,
+                 cudaLaunchKernelEx(&cfg, k_floodfill, vol->d_md, f.depth, f.H, f.W, vol->dp.theta_ppm, vol->d_ff,
+                                    vol->p.max_ff_sweeps, vol->d_status),
+                 "flood-fill launch");
+  if (s != RF_OK) return s;
+  k_dilate<<<blocks, 256, 0, st>>>(vol->d_md, f.H, f.W, mask_out);
+  return check_cuda(vol, cudaGetLastError(), "mask launch");
+}
+
+int floodfill_max_grid(int device) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_floodfill, kFFThreads, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return per_sm * sms;
+}
+
+}  // namespace rf

@@ -1,0 +1,67 @@
+// Host-side state of one volume (the opaque rf_volume of refusion.h).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "rf_internal.cuh"
+
+struct rf_graph_entry {
+  int H, W;
+  double fx, fy, cx, cy;
+  int first;      // first frame: integrate only
+  int profiling;  // graph holds the profiling event records
+  cudaGraphExec_t exec;
+};
+
+struct rf_volume {
+  rf_params p;
+  rf::DevParams dp;
+  rf::DevVol dv;
+  int64_t n_buckets = 0, max_blocks = 0;
+  int max_w = 0, max_h = 0;
+  int device = 0, sm_count = 0;
+  size_t device_bytes = 0;
+
+  // model
+  unsigned long long* d_hash = nullptr;
+  uint2* d_vox = nullptr;
+  uint8_t* d_W = nullptr;
+  int4* d_coords = nullptr;
+  int* d_nblocks = nullptr;
+  unsigned* d_status = nullptr;
+
+  // registration scratch
+  rf::LMState* d_lm = nullptr;
+  float* d_partials = nullptr;
+  int max_partials = 0;
+
+  // mask scratch
+  uint8_t* d_seeds = nullptr;
+  uint8_t* d_md = nullptr;     // M_D during the flood fill
+  unsigned* d_ff = nullptr;    // barrier words + per-sweep change flags
+  int ff_grid = 0;
+
+  // integration scratch
+  rf::IntegState* d_integ = nullptr;
+  int* d_tilemax = nullptr;
+  int4* d_cand = nullptr;
+
+  // whole-frame staging (graph-replayed pipeline reads only these)
+  uint16_t* d_depth = nullptr;
+  uint8_t* d_rgb = nullptr;
+  uint8_t* d_mask = nullptr;
+  double* d_T = nullptr;        // [3][16]: T_in, T_first, T_second
+  rf_track_info* d_info = nullptr;
+
+  unsigned* d_guard = nullptr;  // FP64 re-evaluated seed count of the last mask
+
+  // profiling: events recorded around the stages of the whole-frame calls
+  bool profiling = false;
+  cudaEvent_t ev[rf::EV_COUNT] = {};
+
+  std::vector<rf_graph_entry> graphs;
+  bool use_graphs = true;
+  int64_t frames = 0;
+  std::string last_error;
+};

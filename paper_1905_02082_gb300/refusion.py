@@ -1,0 +1,340 @@
+"""Python binding of librefusion.so (the C ABI in include/refusion.h).
+
+Argument marshalling only: every step of the per-frame path runs in the CUDA
+library.  PyTorch supplies device memory and streams.  If the library is not
+built, importing the binding fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librefusion.so")
+
+RF_OK = 0
+STATUS_NAMES = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_CUDA", 3: "RF_ERR_HASH_FULL", 4: "RF_ERR_POOL_FULL",
+                5: "RF_ERR_NOT_CONVERGED", 6: "RF_ERR_BUFFER_TOO_SMALL", 7: "RF_ERR_OUT_OF_RANGE",
+                8: "RF_ERR_CAPACITY"}
+
+
+class RFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rf_params(C.Structure):
+    _fields_ = [
+        ("voxel_size", C.c_double), ("trunc", C.c_double), ("w_c", C.c_double), ("theta", C.c_double),
+        ("gamma", C.c_double), ("depth_scale", C.c_double), ("d_min", C.c_double), ("d_max", C.c_double),
+        ("z_near", C.c_double), ("w_max", C.c_int), ("lm_iters", C.c_int * 3), ("lm_strides", C.c_int * 3),
+        ("lm_lambda0", C.c_double), ("lm_eps_trans", C.c_double), ("lm_eps_rot", C.c_double),
+        ("lm_min_valid", C.c_int), ("max_ff_sweeps", C.c_int), ("max_candidates", C.c_int64),
+    ]
+
+
+class rf_frame(C.Structure):
+    _fields_ = [("height", C.c_int), ("width", C.c_int), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("depth", C.c_void_p), ("rgb", C.c_void_p)]
+
+
+class rf_track_info(C.Structure):
+    _fields_ = [("evals", C.c_int), ("level_evals", C.c_int * 3), ("converged", C.c_int * 3),
+                ("final_cost", C.c_double), ("final_valid", C.c_int64)]
+
+
+class rf_stats(C.Structure):
+    _fields_ = [("n_blocks", C.c_int64), ("max_blocks", C.c_int64), ("n_buckets", C.c_int64), ("frames", C.c_int64),
+                ("load_factor", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class rf_profile(C.Structure):
+    _fields_ = [("frame_ms", C.c_float), ("track_ms", C.c_float * 2), ("mask_ms", C.c_float),
+                ("integrate_ms", C.c_float), ("integrate_kernel_ms", C.c_float), ("candidates", C.c_int64),
+                ("updated_voxels", C.c_int64), ("new_blocks", C.c_int64), ("guard_pixels", C.c_int64)]
+
+
+# (name, restype, argtypes) of every entry point of refusion.h
+_vp, _i64, _int = C.c_void_p, C.c_int64, C.c_int
+SIGNATURES = [
+    ("rf_default_params", _int, [C.POINTER(rf_params)]),
+    ("rf_create_volume", _int, [C.POINTER(rf_params), _i64, _i64, _int, _int, C.POINTER(_vp)]),
+    ("rf_destroy_volume", _int, [_vp]),
+    ("rf_volume_reset", _int, [_vp]),
+    ("rf_track_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp, _vp, _vp]),
+    ("rf_compute_mask", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
+    ("rf_integrate_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
+    ("rf_process_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp, _vp, _vp]),
+    ("rf_process_frame_host", _int, [_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("rf_extract_mesh", _int, [_vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
+    ("rf_volume_export", _int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, C.POINTER(_i64)]),
+    ("rf_volume_import", _int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    ("rf_volume_stats", _int, [_vp, C.POINTER(rf_stats)]),
+    ("rf_set_profiling", _int, [_vp, _int]),
+    ("rf_get_profile", _int, [_vp, _vp, C.POINTER(rf_profile)]),
+    ("rf_sync_status", _int, [_vp, _vp]),
+    ("rf_last_error", C.c_char_p, [_vp]),
+    ("rf_status_string", C.c_char_p, [_int]),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads librefusion.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"librefusion.so not built at {path}: run paper_1905_02082_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, vol=None):
+    if status != RF_OK:
+        lib = load()
+        msg = lib.rf_last_error(vol)
+        raise RFError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> Optional[int]:
+    """Raw data pointer of a torch tensor / numpy array / None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    return int(t)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---------------------------------------------------------------------------
+# thin same-name wrappers (pointers and sizes in, status checked)
+# ---------------------------------------------------------------------------
+
+def rf_default_params() -> rf_params:
+    p = rf_params()
+    _check(load().rf_default_params(C.byref(p)))
+    return p
+
+
+def rf_create_volume(params: rf_params, n_buckets: int, max_blocks: int, max_width: int, max_height: int):
+    h = C.c_void_p()
+    _check(load().rf_create_volume(C.byref(params), n_buckets, max_blocks, max_width, max_height, C.byref(h)))
+    return h
+
+
+def rf_destroy_volume(h):
+    _check(load().rf_destroy_volume(h))
+
+
+def make_frame(depth, rgb, fx, fy, cx, cy) -> rf_frame:
+    """rf_frame over device tensors depth [H,W] uint16 and rgb [H,W,3] uint8."""
+    H, W = int(depth.shape[0]), int(depth.shape[1])
+    assert tuple(rgb.shape) == (H, W, 3)
+    assert depth.is_contiguous() and rgb.is_contiguous() and depth.is_cuda and rgb.is_cuda
+    return rf_frame(H, W, float(fx), float(fy), float(cx), float(cy), depth.data_ptr(), rgb.data_ptr())
+
+
+def rf_track_frame(h, frame: rf_frame, T_init, mask, T_out, info=None, stream=None):
+    _check(load().rf_track_frame(h, C.byref(frame), _ptr(T_init), _ptr(mask), _ptr(T_out), _ptr(info),
+                                 _stream(stream)), h)
+
+
+def rf_compute_mask(h, frame: rf_frame, T, mask_out, stream=None):
+    _check(load().rf_compute_mask(h, C.byref(frame), _ptr(T), _ptr(mask_out), _stream(stream)), h)
+
+
+def rf_integrate_frame(h, frame: rf_frame, T, mask=None, stream=None):
+    _check(load().rf_integrate_frame(h, C.byref(frame), _ptr(T), _ptr(mask), _stream(stream)), h)
+
+
+def rf_process_frame(h, frame: rf_frame, T_init, T_out, mask_out=None, info=None, stream=None):
+    _check(load().rf_process_frame(h, C.byref(frame), _ptr(T_init), _ptr(T_out), _ptr(mask_out), _ptr(info),
+                                   _stream(stream)), h)
+
+
+def rf_process_frame_host(h, depth: np.ndarray, rgb: np.ndarray, intr, T_init: np.ndarray, T_out: np.ndarray,
+                          mask: Optional[np.ndarray] = None, stream=None):
+    intr = np.ascontiguousarray(intr, dtype=np.float64)
+    _check(load().rf_process_frame_host(h, depth.shape[0], depth.shape[1], _ptr(intr), _ptr(depth), _ptr(rgb),
+                                        _ptr(T_init), _ptr(T_out), _ptr(mask), _stream(stream)), h)
+
+
+def rf_sync_status(h, stream=None):
+    _check(load().rf_sync_status(h, _stream(stream)), h)
+
+
+def rf_volume_stats(h) -> rf_stats:
+    s = rf_stats()
+    _check(load().rf_volume_stats(h, C.byref(s)), h)
+    return s
+
+
+# ---------------------------------------------------------------------------
+# convenience object over one volume
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Intrinsics:
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+
+
+def params(**overrides) -> rf_params:
+    """Default parameters (Tab. I plus readings) with keyword overrides."""
+    p = rf_default_params()
+    for k, v in overrides.items():
+        if k in ("lm_iters", "lm_strides"):
+            setattr(p, k, (C.c_int * 3)(*v))
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Volume:
+    """A device-resident voxel-hashed TSDF volume (one camera stream)."""
+
+    def __init__(self, p: Optional[rf_params] = None, n_buckets: int = 1 << 20, max_blocks: int = 1 << 18,
+                 max_width: int = 640, max_height: int = 480, **overrides):
+        import torch
+        self.torch = torch
+        self.params = p if p is not None else params(**overrides)
+        self.h = rf_create_volume(self.params, n_buckets, max_blocks, max_width, max_height)
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "h", None):
+            rf_destroy_volume(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers -----------------------------------------------------------
+    def _pose(self, T):
+        torch = self.torch
+        if isinstance(T, torch.Tensor) and T.is_cuda and T.dtype == torch.float64 and T.is_contiguous():
+            return T
+        return torch.as_tensor(np.asarray(T, dtype=np.float64).reshape(4, 4), device=self.dev).contiguous()
+
+    def frame(self, depth, rgb, K: Intrinsics) -> rf_frame:
+        return make_frame(depth, rgb, K.fx, K.fy, K.cx, K.cy)
+
+    # -- calls --------------------------------------------------------------
+    def track(self, frame: rf_frame, T_init, mask=None, stream=None):
+        torch = self.torch
+        Tin = self._pose(T_init)
+        Tout = torch.empty(4, 4, dtype=torch.float64, device=self.dev)
+        info = torch.zeros(C.sizeof(rf_track_info), dtype=torch.uint8, device=self.dev)
+        rf_track_frame(self.h, frame, Tin, mask, Tout, info, stream)
+        return Tout, info
+
+    def compute_mask(self, frame: rf_frame, T, out=None, stream=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty(frame.height, frame.width, dtype=torch.uint8, device=self.dev)
+        rf_compute_mask(self.h, frame, self._pose(T), out, stream)
+        return out
+
+    def integrate(self, frame: rf_frame, T, mask=None, stream=None):
+        rf_integrate_frame(self.h, frame, self._pose(T), mask, stream)
+
+    def process(self, frame: rf_frame, T_init, mask_out=None, stream=None):
+        torch = self.torch
+        Tout = torch.empty(4, 4, dtype=torch.float64, device=self.dev)
+        info = torch.zeros(C.sizeof(rf_track_info), dtype=torch.uint8, device=self.dev)
+        rf_process_frame(self.h, frame, self._pose(T_init), Tout, mask_out, info, stream)
+        return Tout, info
+
+    def process_host(self, depth: np.ndarray, rgb: np.ndarray, K: Intrinsics, T_init, want_mask=False,
+                     stream=None):
+        depth = np.ascontiguousarray(depth, dtype=np.uint16)
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        Tin = np.ascontiguousarray(T_init, dtype=np.float64)
+        Tout = np.zeros((4, 4))
+        mask = np.zeros(depth.shape, np.uint8) if want_mask else None
+        rf_process_frame_host(self.h, depth, rgb, [K.fx, K.fy, K.cx, K.cy], Tin, Tout, mask, stream)
+        return Tout, mask
+
+    def sync(self, stream=None):
+        rf_sync_status(self.h, stream)
+
+    def set_profiling(self, enable: bool):
+        _check(load().rf_set_profiling(self.h, 1 if enable else 0), self.h)
+
+    def profile(self, stream=None) -> rf_profile:
+        out = rf_profile()
+        _check(load().rf_get_profile(self.h, _stream(stream), C.byref(out)), self.h)
+        return out
+
+    def stats(self) -> rf_stats:
+        return rf_volume_stats(self.h)
+
+    @staticmethod
+    def info_of(info_tensor) -> rf_track_info:
+        b = info_tensor.cpu().numpy().tobytes()
+        return rf_track_info.from_buffer_copy(b)
+
+    def export(self):
+        lib = load()
+        n = C.c_int64()
+        _check(lib.rf_volume_export(self.h, 0, None, None, None, None, None, C.byref(n)), self.h)
+        nb = n.value
+        snap = dict(coords=np.zeros((nb, 3), np.int32), F=np.zeros((nb, 512), np.float32),
+                    W=np.zeros((nb, 512), np.uint8), rgb=np.zeros((nb, 512, 3), np.uint8),
+                    wc=np.zeros((nb, 512), np.uint8))
+        if nb:
+            _check(lib.rf_volume_export(self.h, nb, _ptr(snap["coords"]), _ptr(snap["F"]), _ptr(snap["W"]),
+                                        _ptr(snap["rgb"]), _ptr(snap["wc"]), C.byref(n)), self.h)
+        return snap
+
+    def import_(self, snap):
+        c = np.ascontiguousarray(snap["coords"], dtype=np.int32)
+        F = np.ascontiguousarray(snap["F"], dtype=np.float32)
+        W = np.ascontiguousarray(snap["W"], dtype=np.uint8)
+        rgb = np.ascontiguousarray(snap["rgb"], dtype=np.uint8)
+        wc = np.ascontiguousarray(snap["wc"], dtype=np.uint8)
+        _check(load().rf_volume_import(self.h, len(c), _ptr(c), _ptr(F), _ptr(W), _ptr(rgb), _ptr(wc)), self.h)
+
+    def reset(self):
+        _check(load().rf_volume_reset(self.h), self.h)
+
+    def extract_mesh(self, stream=None):
+        torch = self.torch
+        lib = load()
+        n = C.c_int64()
+        _check(lib.rf_extract_mesh(self.h, None, None, 0, C.byref(n), _stream(stream)), self.h)
+        nt = n.value
+        verts = torch.empty(max(nt, 1), 3, 3, dtype=torch.float32, device=self.dev)
+        cols = torch.empty(max(nt, 1), 3, 3, dtype=torch.uint8, device=self.dev)
+        if nt:
+            _check(lib.rf_extract_mesh(self.h, verts.data_ptr(), cols.data_ptr(), nt, C.byref(n), _stream(stream)),
+                   self.h)
+        return verts[:nt], cols[:nt]

@@ -1,0 +1,87 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+exports every function declared in include/refusion.h, the binding declares
+the same set, and host-side argument handling works without a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1905_02082_gb300 import build as B
+    return B.build()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "refusion.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(rf_[a-z_]+)\s*\(", text))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ("rf_create_volume", "rf_track_frame", "rf_integrate_frame", "rf_extract_mesh", "rf_compute_mask",
+              "rf_process_frame", "rf_volume_export", "rf_volume_import", "rf_destroy_volume", "rf_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (rf_[a-z_]+)\b", out))
+    missing = _declared_functions() - exported
+    assert not missing, missing
+    lib = ctypes.CDLL(lib_path)
+    for n in _declared_functions():
+        getattr(lib, n)
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_1905_02082_gb300.refusion as R
+    assert {s[0] for s in R.SIGNATURES} == _declared_functions()
+
+
+def test_default_params_are_table_1(lib_path):
+    import json
+    import paper_1905_02082_gb300.refusion as R
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "tab1_parameters.json")))
+    p = R.rf_default_params()
+    for k in ("voxel_size", "trunc", "w_c", "theta", "gamma"):
+        assert getattr(p, k) == g[k]
+
+
+def test_struct_sizes_match_header(lib_path, tmp_path):
+    """ctypes layouts equal the C layouts (compiled with the host compiler)."""
+    import paper_1905_02082_gb300.refusion as R
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "refusion.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(rf_params), sizeof(rf_frame),'
+                   ' sizeof(rf_track_info), sizeof(rf_stats), offsetof(rf_params, max_candidates));'
+                   'printf("%zu\\n", sizeof(rf_profile));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    assert got == [ctypes.sizeof(R.rf_params), ctypes.sizeof(R.rf_frame), ctypes.sizeof(R.rf_track_info),
+                   ctypes.sizeof(R.rf_stats), R.rf_params.max_candidates.offset, ctypes.sizeof(R.rf_profile)]
+
+
+def test_argument_errors_are_reported_on_the_host(lib_path):
+    import paper_1905_02082_gb300.refusion as R
+    lib = R.load()
+    p = R.rf_default_params()
+    h = ctypes.c_void_p()
+    # invalid parameters are rejected before any CUDA call
+    bad = R.rf_default_params()
+    bad.voxel_size = 0.0123456789
+    assert lib.rf_create_volume(ctypes.byref(bad), 1 << 10, 100, 64, 64, ctypes.byref(h)) == 1
+    assert b"micrometre" in lib.rf_last_error(None)
+    assert lib.rf_create_volume(ctypes.byref(p), 1000, 100, 64, 64, ctypes.byref(h)) == 1  # not a power of two
+    assert lib.rf_create_volume(None, 1 << 10, 100, 64, 64, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.rf_destroy_volume(None) == 0
+    assert lib.rf_track_frame(None, None, None, None, None, None, None) == 1
+    assert lib.rf_status_string(3) == b"hash table full"

@@ -583,9 +583,11 @@ def test_gamma_limits(oracle_mod):
     T = O.se3_exp(np.array([0.03, 0.0, -0.02, 0.0, 0.01, 0.0])) @ corner_pose(2.5)
     d, rgb, _ = render_frame([ROOM], CAM_TINY, corner_pose(2.5))
     f = _frame(O, d, rgb, CAM_TINY)
-    for gamma in (1.0, 0.0, 0.5):
+    snap32 = dict(snap)
+    snap32["F"] = snap["F"].astype(np.float32).astype(np.float64)  # float32(tau) > tau in FP64
+    for gamma, sn in ((1.0, snap), (1.0, snap32), (0.0, snap), (0.5, snap)):
         vol = O.OracleVolume(voxel_size=0.02, trunc=0.1, gamma=gamma)
-        vol.import_(snap)
+        vol.import_(sn)
         r, seeds = vol.residuals(f, T)
         if gamma == 1.0:
             assert seeds.sum() == 0 and r.max() <= 0.1 ** 2
