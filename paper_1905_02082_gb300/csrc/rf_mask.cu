@@ -17,6 +17,7 @@
 //                no tile changes; at most max_ff_sweeps sweeps.
 //   k_dilate     final mask = 3x3 dilation of M_D.
 #include <cmath>
+#include <mutex>
 
 #include "rf_volume.hpp"
 
@@ -274,4 +275,87 @@ int floodfill_max_grid(int device) {
   return per_sm * sms;
 }
 
+// ---------------------------------------------------------------------------
+// Mask without any allocation: the per-call scratch of rf_compute_mask (seed
+// image, flood-fill working mask, barrier words, per-sweep change flags and the
+// guard counter) lives in one file-scope device array instead of the buffers
+// the volume owns.  Every GPU that loads this library holds the array (about
+// 1.9 MB) until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxPixels = 1280 * 720;  // largest frame: 921,600 pixels
+constexpr int kNoAllocMaxSweeps = 4096;         // flood-fill sweep bound of this entry point
+constexpr size_t kNoAllocWordsOff = 2 * (size_t)kNoAllocMaxPixels;  // multiple of 256
+constexpr size_t kNoAllocWords = 2 + kNoAllocMaxSweeps + 1;         // barrier, change flags, guard count
+constexpr size_t kNoAllocBytes = kNoAllocWordsOff + sizeof(unsigned) * kNoAllocWords;
+
+static __device__ __align__(256) unsigned char g_mask_scratch[kNoAllocBytes];
+
+// Device address of g_mask_scratch, looked up once per device with that
+// device current.  In host code the symbol is only a host-side stand-in.
+static void* mask_scratch_address(int device, cudaError_t* err) {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  *err = cudaSuccess;
+  if (device < 0 || device >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[device]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_mask_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    addr[device] = p;
+  }
+  return addr[device];
+}
+
 }  // namespace rf
+
+using namespace rf;
+
+extern "C" rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* frame, const double* T_dev,
+                                             uint8_t* mask_dev, void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (!frame_ok(vol, frame)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
+  if (!T_dev || !mask_dev) return set_error(vol, RF_ERR_INVALID_ARG, "NULL pose or mask");
+  if ((int64_t)frame->height * frame->width > kNoAllocMaxPixels)
+    return set_error(vol, RF_ERR_INVALID_ARG,
+                     "rf_compute_mask_noalloc: frame of %d x %d pixels exceeds the static scratch limit of %d pixels",
+                     frame->width, frame->height, kNoAllocMaxPixels);
+  int device = 0;
+  rf_status s = check_cuda(vol, cudaGetDevice(&device), "current device");
+  if (s) return s;
+  cudaError_t e;
+  unsigned char* base = static_cast<unsigned char*>(mask_scratch_address(device, &e));
+  if (!base) return check_cuda(vol, e, "cudaGetSymbolAddress(mask scratch)");
+  uint8_t* seeds = base;
+  uint8_t* md = base + kNoAllocMaxPixels;
+  unsigned* ff = reinterpret_cast<unsigned*>(base + kNoAllocWordsOff);
+  unsigned* guard = ff + 2 + kNoAllocMaxSweeps;
+  const int sweeps = vol->p.max_ff_sweeps < kNoAllocMaxSweeps ? vol->p.max_ff_sweeps : kNoAllocMaxSweeps;
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevFrame f = make_dev_frame(frame);
+  const int n = f.H * f.W;
+  const int blocks = (n + 255) / 256;
+  // the array keeps the previous call's contents: zero the words that count
+  if ((s = check_cuda(vol, cudaMemsetAsync(ff, 0, sizeof(unsigned) * kNoAllocWords, st), "scratch clear"))) return s;
+  k_seeds<<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard);
+  k_erode<<<blocks, 256, 0, st>>>(seeds, f.H, f.W, md);
+  const int ntiles = ((f.W + kFFW - 1) / kFFW) * ((f.H + kFFH - 1) / kFFH);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ntiles < vol->ff_grid ? ntiles : vol->ff_grid);
+  cfg.blockDim = dim3(kFFThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if ((s = check_cuda(vol, cudaLaunchKernelEx(&cfg, k_floodfill, md, f.depth, f.H, f.W, vol->dp.theta_ppm, ff,
+                                              sweeps, vol->d_status),
+                      "flood-fill launch")))
+    return s;
+  k_dilate<<<blocks, 256, 0, st>>>(md, f.H, f.W, mask_dev);
+  return check_cuda(vol, cudaGetLastError(), "mask launch");
+}

@@ -68,6 +68,7 @@ SIGNATURES = [
     ("rf_volume_reset", _int, [_vp]),
     ("rf_track_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp, _vp, _vp]),
     ("rf_compute_mask", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
+    ("rf_compute_mask_noalloc", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
     ("rf_integrate_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
     ("rf_process_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp, _vp, _vp]),
     ("rf_process_frame_host", _int, [_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -164,6 +165,11 @@ def rf_track_frame(h, frame: rf_frame, T_init, mask, T_out, info=None, stream=No
 
 def rf_compute_mask(h, frame: rf_frame, T, mask_out, stream=None):
     _check(load().rf_compute_mask(h, C.byref(frame), _ptr(T), _ptr(mask_out), _stream(stream)), h)
+
+
+def rf_compute_mask_noalloc(h, frame: rf_frame, T, mask_out, stream=None):
+    """rf_compute_mask with its scratch in a static device array (no allocation)."""
+    _check(load().rf_compute_mask_noalloc(h, C.byref(frame), _ptr(T), _ptr(mask_out), _stream(stream)), h)
 
 
 def rf_integrate_frame(h, frame: rf_frame, T, mask=None, stream=None):
