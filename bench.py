@@ -293,6 +293,12 @@ def main():
                "steps": n_e2e, "api": "rf_process_frame_host"}
         vol2.close()
 
+    # kernels of this library per whole frame (graph nodes): per registration one
+    # init, one final, and per level (1 + iters) accumulation + LM-step pairs;
+    # mask: seeds, erosion, flood fill, dilation; integration: 5 kernels
+    p = vol.params
+    per_reg = 2 + sum(2 * (1 + p.lm_iters[l]) for l in range(3))
+    launches_per_frame = 2 * per_reg + 4 + 5
     if rank == 0:
         st = vol.stats()
         line = {
@@ -315,7 +321,8 @@ def main():
                      "guard_pixels": statistics.mean(p.guard_pixels for p in profs)},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": None,
+            "gpu_launches": launches_per_frame * args.steps,
+            "gpu_launches_per_frame": launches_per_frame,
             "clocks": clk,
             "wall_s_timed": wall,
         }

@@ -14,6 +14,7 @@
 
 namespace rf {
 int floodfill_max_grid(int device);
+int register_max_grid(int device);
 
 static thread_local std::string g_create_error;
 
@@ -51,6 +52,10 @@ DevFrame make_dev_frame(const rf_frame* f) {
   d.fyq = llround(f->fy * 256.0);
   d.cxq = llround((f->cx + 0.5) * 256.0);
   d.cyq = llround((f->cy + 0.5) * 256.0);
+  // |estimate - exact| <= 6e-7 |f x / z| + 2.5e-4 px, with |f x / z| bounded by
+  // the image extent around the principal point (see the integration kernel)
+  d.amb_u = (float)(4.0 * (6e-7 * 2.0 * (f->width + std::fabs(f->cx)) + 2.5e-4));
+  d.amb_v = (float)(4.0 * (6e-7 * 2.0 * (f->height + std::fabs(f->cy)) + 2.5e-4));
   d.depth = f->depth;
   d.rgb = f->rgb;
   return d;
@@ -119,6 +124,7 @@ DevParams derive(const rf_params& p) {
   d.tau = (float)p.trunc;
   d.w_c = (float)p.w_c;
   d.gamma_tau2 = (float)(p.gamma * p.trunc * p.trunc);
+  d.gamma_tau2_f = (float)((p.gamma * p.trunc) * p.trunc);
   d.inv_depth_scale = (float)(1.0 / p.depth_scale);
   d.z_near = (float)p.z_near;
   d.d_max = (float)p.d_max;
@@ -328,7 +334,7 @@ rf_status rf_destroy_volume(rf_volume* vol) {
   for (auto& e : vol->ev)
     if (e) cudaEventDestroy(e);
   void* dev[] = {vol->d_hash, vol->d_vox,  vol->d_W,       vol->d_coords, vol->d_nblocks, vol->d_status,
-                 vol->d_lm,   vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
+                 vol->d_regbar, vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
                  vol->d_tilemax, vol->d_cand, vol->d_depth, vol->d_rgb,   vol->d_mask,    vol->d_T, vol->d_info,
                  vol->d_guard};
   for (void* p : dev)
@@ -364,14 +370,20 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
     return s;
   }
   const size_t npix = (size_t)max_width * max_height;
-  vol->max_partials = 4 * vol->sm_count;
+  vol->reg_grid = register_max_grid(vol->device);
+  if (vol->reg_grid > vol->sm_count) vol->reg_grid = vol->sm_count;
+  if (vol->reg_grid < 1) {
+    s = set_error(nullptr, RF_ERR_CUDA, "registration kernel cannot be resident on this device");
+    delete vol;
+    return s;
+  }
   const size_t ntiles = ((size_t)(max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
   const size_t nslots = (size_t)n_buckets * kSlots;
   if ((s = dalloc(vol, &vol->d_hash, nslots, "hash")) || (s = dalloc(vol, &vol->d_vox, (size_t)max_blocks * kBV, "voxels")) ||
       (s = dalloc(vol, &vol->d_W, (size_t)max_blocks * kBV, "weights")) ||
       (s = dalloc(vol, &vol->d_coords, (size_t)max_blocks, "coords")) || (s = dalloc(vol, &vol->d_nblocks, 1, "pool")) ||
-      (s = dalloc(vol, &vol->d_status, 1, "status")) || (s = dalloc(vol, &vol->d_lm, 1, "lm")) ||
-      (s = dalloc(vol, &vol->d_partials, (size_t)vol->max_partials * kPartialStride, "partials")) ||
+      (s = dalloc(vol, &vol->d_status, 1, "status")) || (s = dalloc(vol, &vol->d_regbar, 2, "barrier")) ||
+      (s = dalloc(vol, &vol->d_partials, (size_t)2 * 29 * vol->reg_grid + 2, "partials")) ||
       (s = dalloc(vol, &vol->d_seeds, npix, "seeds")) || (s = dalloc(vol, &vol->d_md, npix, "mask work")) ||
       (s = dalloc(vol, &vol->d_ff, (size_t)p->max_ff_sweeps + 2, "flood-fill words")) ||
       (s = dalloc(vol, &vol->d_integ, 1, "integ")) || (s = dalloc(vol, &vol->d_tilemax, ntiles, "tiles")) ||

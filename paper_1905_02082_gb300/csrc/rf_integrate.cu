@@ -20,8 +20,8 @@
 //   k_cull         conservative per-block frustum/depth test, warp-aggregated
 //                  append to the candidate list                     (block/thread)
 //   k_integrate    exact per-voxel predicate, lock-free hash insert of blocks
-//                  with updates, read-modify-write of updated voxels (block/CTA,
-//                  persistent, blocks taken from an atomic work counter)
+//                  with updates, read-modify-write of updated voxels (one warp
+//                  per block, persistent grid, static round-robin)
 #include <cmath>
 
 #include "rf_volume.hpp"
@@ -29,24 +29,26 @@
 namespace rf {
 namespace {
 
+// Quantised pose (one entry per lane: conversions run on the FP64 pipe, so
+// they are spread over lanes) and reset of the per-frame counters.
 __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st) {
-  if (threadIdx.x != 0) return;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      st->A[i * 3 + j] = llround(T[j * 4 + i] * 1073741824.0);
-      st->R[i * 3 + j] = (float)T[i * 4 + j];
-    }
-  for (int i = 0; i < 3; ++i) {
-    st->tq[i] = llround(T[i * 4 + 3] * 1e6);
-    st->t[i] = (float)T[i * 4 + 3];
+  const int a = threadIdx.x;
+  if (a < 9) {
+    const int i = a / 3, j = a % 3;
+    st->A[a] = llround(T[j * 4 + i] * 1073741824.0);  // world -> camera rotation R^T, 2^30 scale
+    st->R[a] = (float)T[i * 4 + j];
+  } else if (a < 12) {
+    st->tq[a - 9] = llround(T[(a - 9) * 4 + 3] * 1e6);
+    st->t[a - 9] = (float)T[(a - 9) * 4 + 3];
+  } else if (a == 12) {
+    st->max_um = -1;
+    st->n_cand = 0;
+    st->work = 0;
+    st->total = 0;
+    st->clipped = 0;
+    st->new_blocks = 0;
+    st->updated = 0ull;
   }
-  st->max_um = -1;
-  st->n_cand = 0;
-  st->work = 0;
-  st->total = 0;
-  st->clipped = 0;
-  st->new_blocks = 0;
-  st->updated = 0ull;
 }
 
 __global__ void __launch_bounds__(256) k_tilemax(DevFrame f, DevParams p, const uint8_t* __restrict__ mask,
@@ -77,41 +79,51 @@ __global__ void __launch_bounds__(256) k_tilemax(DevFrame f, DevParams p, const 
 // non-finite pose).
 constexpr long long kMaxSearchBlocks = 1ll << 28;
 
+// Block range of the truncated frustum z in (z_near, zfar], zfar =
+// min(max valid depth + tau, d_max), over the pixel rectangle.  Float math on
+// 8 lanes (one frustum corner each); the 2-voxel margin covers its rounding.
 __global__ void k_integ_aabb(const double* __restrict__ T, DevFrame f, DevParams p, IntegState* st) {
-  if (threadIdx.x != 0) return;
-  if (st->max_um < 0) {
-    st->total = 0;
+  const int lane = threadIdx.x;
+  const int max_um = st->max_um;
+  if (max_um < 0) {
+    if (lane == 0) st->total = 0;
     return;
   }
-  for (int i = 0; i < 12; ++i)
-    if (!isfinite(T[i])) {
-      st->total = 0;
-      st->clipped = 1;
-      return;
+  const float zfar = fminf((float)max_um * 1e-6f + p.tau, (float)p.dmax_um * 1e-6f);
+  bool finite = true;
+  for (int i = 0; i < 9; ++i) finite &= isfinite(st->R[i]) != 0;
+  for (int i = 0; i < 3; ++i) finite &= isfinite(st->t[i]) != 0;
+  float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+  if (lane < 8) {
+    const float z = (lane & 4) ? zfar : p.z_near;
+    const float u = (lane & 1) ? (float)f.W - 0.5f : -0.5f, v = (lane & 2) ? (float)f.H - 0.5f : -0.5f;
+    const float x = (u - f.cx) * f.ifx * z, y = (v - f.cy) * f.ify * z;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float w = st->R[i * 3] * x + st->R[i * 3 + 1] * y + st->R[i * 3 + 2] * z + st->t[i];
+      lo[i] = w;
+      hi[i] = w;
     }
-  const double zfar = fmin(st->max_um * 1e-6 + p.tau_d, (double)p.dmax_um * 1e-6);
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  const double us[2] = {-0.5, f.W - 0.5}, vs[2] = {-0.5, f.H - 0.5};
-  const double zs[2] = {(double)p.z_near, zfar};
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b)
-      for (int c = 0; c < 2; ++c) {
-        const double z = zs[a];
-        const double x = (us[b] - f.cxd) / f.fxd * z, y = (vs[c] - f.cyd) / f.fyd * z;
-        for (int i = 0; i < 3; ++i) {
-          const double w = T[i * 4 + 0] * x + T[i * 4 + 1] * y + T[i * 4 + 2] * z + T[i * 4 + 3];
-          lo[i] = fmin(lo[i], w);
-          hi[i] = fmax(hi[i], w);
-        }
-      }
-  const double bs = 8.0 * p.voxel_d, margin = 2.0 * p.voxel_d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lo[i] = fminf(lo[i], __shfl_xor_sync(0xffffffffu, lo[i], o));
+      hi[i] = fmaxf(hi[i], __shfl_xor_sync(0xffffffffu, hi[i], o));
+    }
+  if (lane != 0) return;
+  const float bs = 8.0f * p.voxel, margin = 2.0f * p.voxel;
   long long total = 1;
-  bool clipped = false;
-  for (int i = 0; i < 3; ++i) {
-    const double f0 = fmax(fmin(floor((lo[i] - margin) / bs), 1e9), -1e9);
-    const double f1 = fmax(fmin(floor((hi[i] + margin) / bs), 1e9), -1e9);
-    long long b0 = (long long)f0;
-    long long b1 = (long long)f1;
+  bool clipped = !finite;
+  for (int i = 0; i < 3 && !clipped; ++i) {
+    const float f0 = fmaxf(fminf(floorf((lo[i] - margin) / bs), 1e9f), -1e9f);
+    const float f1 = fmaxf(fminf(floorf((hi[i] + margin) / bs), 1e9f), -1e9f);
+    if (!(f0 == f0) || !(f1 == f1)) {
+      clipped = true;
+      break;
+    }
+    long long b0 = (long long)f0, b1 = (long long)f1;
     if (b0 < -kMaxCoord) { b0 = -kMaxCoord; clipped = true; }
     if (b1 > kMaxCoord) { b1 = kMaxCoord; clipped = true; }
     if (b1 < b0) b1 = b0 - 1;
@@ -119,12 +131,9 @@ __global__ void k_integ_aabb(const double* __restrict__ T, DevFrame f, DevParams
     st->dims[i] = (int)(b1 - b0 + 1);
     total *= (b1 - b0 + 1);
   }
-  if (total > kMaxSearchBlocks) {
-    total = 0;
-    clipped = true;
-  }
+  if (!finite || total > kMaxSearchBlocks) total = 0;
   st->total = total > 0 ? total : 0;
-  st->zfar = (float)zfar;
+  st->zfar = zfar;
   st->clipped = clipped ? 1 : 0;  // blocks beyond the key range cannot be stored (reported by k_cull)
 }
 
@@ -214,41 +223,60 @@ __global__ void __launch_bounds__(256) k_cull(DevFrame f, DevParams p, IntegStat
   }
 }
 
-// floor(num / den) for den > 0 when it lies in [0, n), else -1.  A float
-// guess is corrected and verified with exact int64 products.
-__device__ __forceinline__ int pixel_of(long long num, long long den, int n) {
-  float g = floorf(__fdividef(__ll2float_rn(num), __ll2float_rn(den)));
-  g = fminf(fmaxf(g, -2.0f), (float)n + 1.0f);
-  long long u = (long long)g;
+// floor(num / den) for den > 0 when it lies in [0, n), else -1.  `guess` is
+// a float estimate of num / den (within one unit when the result is in
+// range); it is corrected and verified with exact int64 products.  No
+// int64 <-> float conversion is used: those run on the FP64 pipe.
+__device__ __forceinline__ int pixel_of(float guess, long long num, long long den, int n) {
+  const float g = fminf(fmaxf(floorf(guess), -2.0f), (float)n + 1.0f);
+  long long u = (long long)(int)g;
   if (u * den > num) u -= 1;
   else if ((u + 1) * den <= num) u += 1;
   if (u * den > num || (u + 1) * den <= num) return -1;
   return (u >= 0 && u < n) ? (int)u : -1;
 }
 
-struct Obs {
-  float x;
-  int pix;
-  bool band;
-};
-
-__device__ __forceinline__ bool observe(long long Cx, long long Cy, long long Cz, const DevFrame& f,
-                                        const DevParams& p, const uint8_t* __restrict__ mask, Obs* o) {
-  if (Cz <= p.znear_tick || Cz > p.dmax_tick) return false;
+// Exact nearest pixel of a voxel with camera coordinates (Cx, Cy, Cz) in
+// ticks, or -1 when z is outside (z_near, d_max] or the pixel is outside the
+// image.  (xf, yf, zf): float estimates used only for the guess.
+__device__ __forceinline__ int voxel_pixel(long long Cx, long long Cy, long long Cz, float xf, float yf, float zf,
+                                           const DevFrame& f, const DevParams& p, float fxg, float fyg, float cxg,
+                                           float cyg) {
+  if (Cz <= p.znear_tick || Cz > p.dmax_tick) return -1;
   const long long den = Cz << 8;
-  const int u = pixel_of(f.fxq * Cx + f.cxq * Cz, den, f.W);
-  if (u < 0) return false;
-  const int v = pixel_of(f.fyq * Cy + f.cyq * Cz, den, f.H);
-  if (v < 0) return false;
-  const int idx = v * f.W + u;
-  const unsigned raw = __ldg(f.depth + idx);
+  const float iz = __fdividef(1.0f, zf);
+  const int u = pixel_of(fxg * xf * iz + cxg, f.fxq * Cx + f.cxq * Cz, den, f.W);
+  if (u < 0) return -1;
+  const int v = pixel_of(fyg * yf * iz + cyg, f.fyq * Cy + f.cyq * Cz, den, f.H);
+  if (v < 0) return -1;
+  return v * f.W + u;
+}
+
+// Fast path of the nearest-pixel rounding: floor of the float estimate when
+// it is farther than `amb` from a rounding boundary (then provably equal to
+// the exact floor), else kAmbiguous.  Out-of-range results give -1.
+constexpr int kAmbiguous = -2;
+__device__ __forceinline__ int pixel_fast(float est, float amb, int n) {
+  const float fl = floorf(est);
+  const float fr = est - fl;
+  if (fr < amb || fr > 1.0f - amb) return kAmbiguous;
+  return (fl >= 0.0f && fl < (float)n) ? (int)fl : -1;
+}
+
+// Update value of a voxel whose pixel has raw depth `raw`: false when the
+// voxel is not updated (invalid pixel or occluded: sdf < -tau).
+__device__ __forceinline__ bool voxel_value(unsigned raw, long long Cz, const DevParams& p, float* x, bool* band) {
   if (!pixel_valid(p, raw)) return false;
-  if (mask && __ldg(mask + idx)) return false;
   const long long sdf = (long long)raw * p.du_um * 1024 - Cz;
   if (sdf < -p.tau_tick) return false;
-  o->band = sdf <= p.tau_tick;
-  o->x = o->band ? __ll2float_rn(sdf) * 9.765625e-10f : p.tau;
-  o->pix = idx;
+  *band = sdf <= p.tau_tick;
+  if (*band) {
+    // |sdf| <= tau_tick: a 32-bit conversion (exact below 2^31 ticks = 2.1 m)
+    *x = p.tau_tick < (1ll << 31) ? __int2float_rn((int)sdf) * 9.765625e-10f
+                                  : __int2float_rn((int)(sdf >> 8)) * 2.5e-7f;
+  } else {
+    *x = p.tau;
+  }
   return true;
 }
 
@@ -290,108 +318,173 @@ __device__ int hash_insert(const DevVol& v, int bx, int by, int bz, bool* is_new
   return -1;
 }
 
-constexpr int kIntegThreads = 256;
-constexpr int kVPT = kBV / kIntegThreads;  // voxels per thread
+constexpr int kIntegThreads = 128;  // 4 warps; one warp integrates one block at a time
+constexpr int kIntegWarps = kIntegThreads / 32;
+constexpr int kVPL = kBV / 32;       // 16 voxels per lane: voxel lane + 32 j
 
+// One warp per candidate block (static round-robin over all warps): no CTA
+// barriers.  Lane l owns voxels (x, y, z) = (l & 7, (l >> 3) + 4 (j & 1), j >> 1),
+// j = 0..15, whose exact camera coordinates follow from the block's by int64
+// additions.  Per block: (1) nearest pixels of the 16 voxels (float estimate,
+// exact integer path only near rounding boundaries), (2) depth loads four at
+// a time and the exact truncation tests, (3) hash lookup (first bucket
+// prefetched by lanes 0-3) or insert, (4) read-modify-write of the updated
+// voxels.  Per-voxel values are staged in shared memory, not registers.
 __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame f, DevParams p,
                                                              const uint8_t* __restrict__ mask, IntegState* st,
                                                              const int4* __restrict__ cand, long long max_cand) {
-  __shared__ long long sA[9], sT[3];
-  __shared__ long long sC0[3];
-  __shared__ int s_idx, s_pool, s_new;
-  if (threadIdx.x < 9) sA[threadIdx.x] = st->A[threadIdx.x];
-  if (threadIdx.x < 3) sT[threadIdx.x] = st->tq[threadIdx.x];
+  __shared__ int s_px[kIntegWarps][kVPL][32];    // pixel index | band << 31, or -1
+  __shared__ float s_x[kIntegWarps][kVPL][32];   // update value
+  __shared__ long long A[9], tq[3];              // quantised pose
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int(*spx)[32] = s_px[wid];
+  float(*sx)[32] = s_x[wid];
+  if (threadIdx.x < 9) A[threadIdx.x] = st->A[threadIdx.x];
+  if (threadIdx.x < 3) tq[threadIdx.x] = st->tq[threadIdx.x];
   __syncthreads();
   const long long n_cand = min((long long)*(volatile int*)&st->n_cand, max_cand);
-  // per-thread lattice offsets A * (v_um * o) of the voxels this thread owns
-  long long off[kVPT][3];
+  const long long lx = (long long)(lane & 7) * p.v_um, ly = (long long)(lane >> 3) * p.v_um;
+  long long O[3], SY4[3], SZ[3];
+  float SY4f[3], SZf[3];
 #pragma unroll
-  for (int j = 0; j < kVPT; ++j) {
-    const int li = threadIdx.x + j * kIntegThreads;
-    const long long o[3] = {(long long)(li & 7) * p.v_um, (long long)((li >> 3) & 7) * p.v_um,
-                            (long long)(li >> 6) * p.v_um};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) off[j][i] = sA[i * 3] * o[0] + sA[i * 3 + 1] * o[1] + sA[i * 3 + 2] * o[2];
+  for (int i = 0; i < 3; ++i) {
+    O[i] = A[i * 3] * lx + A[i * 3 + 1] * ly;
+    SY4[i] = A[i * 3 + 1] * (4 * p.v_um);
+    SZ[i] = A[i * 3 + 2] * p.v_um;
+    SY4f[i] = (float)(SY4[i] >> 20);  // float estimates in ticks, converted once per thread
+    SZf[i] = (float)(SZ[i] >> 20);
   }
+  const float fxg = (float)f.fxq * (1.0f / 256.0f), fyg = (float)f.fyq * (1.0f / 256.0f);
+  const float cxg = (float)f.cxq * (1.0f / 256.0f), cyg = (float)f.cyq * (1.0f / 256.0f);
   const unsigned nan_bits = 0x7fc00000u;
-  unsigned my_updated = 0;
-  for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(&st->work, 1);
-    __syncthreads();
-    const int ci = s_idx;
-    if (ci >= n_cand) break;
+  const long long warp0 = ((long long)blockIdx.x * kIntegThreads + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * kIntegThreads) >> 5;
+  unsigned my_updated = 0, my_new = 0;
+  for (long long ci = warp0; ci < n_cand; ci += nwarps) {
     const int4 b = cand[ci];
-    if (threadIdx.x < 3) {
-      const int i = threadIdx.x;
-      const long long d0 = (long long)b.x * 8 * p.v_um - sT[0];
-      const long long d1 = (long long)b.y * 8 * p.v_um - sT[1];
-      const long long d2 = (long long)b.z * 8 * p.v_um - sT[2];
-      sC0[i] = sA[i * 3] * d0 + sA[i * 3 + 1] * d1 + sA[i * 3 + 2] * d2;
-    }
-    __syncthreads();
-    Obs ob[kVPT];
-    bool pass[kVPT];
-    int any = 0;
+    const unsigned long long key = pack_key(b.x, b.y, b.z);
+    const bool in_range = coord_ok(b.x, b.y, b.z);
+    const unsigned long long bucket = mix64(key) & v.bucket_mask;
+    unsigned long long e = kEmpty;
+    if (lane < kSlots && in_range) e = __ldcg(v.hash + bucket * kSlots + lane);  // prefetch
+    // exact camera coordinates of voxel (lane & 7, lane >> 3, 0) of this block
+    long long c0[3];
+    float c0f[3];
 #pragma unroll
-    for (int j = 0; j < kVPT; ++j) {
-      const long long Cx = (sC0[0] + off[j][0]) >> 20;
-      const long long Cy = (sC0[1] + off[j][1]) >> 20;
-      const long long Cz = (sC0[2] + off[j][2]) >> 20;
-      pass[j] = observe(Cx, Cy, Cz, f, p, mask, &ob[j]);
-      any |= pass[j];
+    for (int i = 0; i < 3; ++i) {
+      const long long d0 = (long long)b.x * 8 * p.v_um - tq[0], d1 = (long long)b.y * 8 * p.v_um - tq[1],
+                      d2 = (long long)b.z * 8 * p.v_um - tq[2];
+      c0[i] = A[i * 3] * d0 + A[i * 3 + 1] * d1 + A[i * 3 + 2] * d2 + O[i];
+      c0f[i] = (float)(c0[i] >> 20);
     }
-    if (!__syncthreads_or(any)) continue;
-#pragma unroll
-    for (int j = 0; j < kVPT; ++j) my_updated += pass[j];
-    if (threadIdx.x == 0) {
-      bool is_new;
-      s_pool = hash_insert(v, b.x, b.y, b.z, &is_new);
-      s_new = is_new;
-      if (is_new) atomicAdd(&st->new_blocks, 1);
+    // 1) nearest pixel of each voxel
+#pragma unroll 2
+    for (int j = 0; j < kVPL; ++j) {
+      const int h = j & 1, zz = j >> 1;
+      const long long Cz = (c0[2] + (h ? SY4[2] : 0ll) + zz * SZ[2]) >> 20;
+      int pix = -1;
+      if (Cz > p.znear_tick && Cz <= p.dmax_tick) {
+        const float xf = c0f[0] + (h ? SY4f[0] : 0.0f) + (float)zz * SZf[0];
+        const float yf = c0f[1] + (h ? SY4f[1] : 0.0f) + (float)zz * SZf[1];
+        const float zf = c0f[2] + (h ? SY4f[2] : 0.0f) + (float)zz * SZf[2];
+        const float iz = __frcp_rn(zf);
+        const int u = pixel_fast(fxg * xf * iz + cxg, f.amb_u, f.W);
+        const int vv = pixel_fast(fyg * yf * iz + cyg, f.amb_v, f.H);
+        pix = (u == kAmbiguous || vv == kAmbiguous) ? kAmbiguous : ((u < 0 || vv < 0) ? -1 : vv * f.W + u);
+        if (pix == kAmbiguous) {
+          const long long Cx = (c0[0] + (h ? SY4[0] : 0ll) + zz * SZ[0]) >> 20;
+          const long long Cy = (c0[1] + (h ? SY4[1] : 0ll) + zz * SZ[1]) >> 20;
+          pix = voxel_pixel(Cx, Cy, Cz, xf, yf, zf, f, p, fxg, fyg, cxg, cyg);
+        }
+      }
+      spx[j][lane] = pix;
     }
-    __syncthreads();
-    const int pool = s_pool;
+    // 2) depth (and mask) loads, four voxels at a time, and the exact tests
+    unsigned passbits = 0;
+#pragma unroll 4
+    for (int j = 0; j < kVPL; ++j) {
+      const int pix = spx[j][lane];
+      unsigned raw = pix >= 0 ? (unsigned)__ldg(f.depth + pix) : 0u;
+      if (mask && pix >= 0 && __ldg(mask + pix)) raw = 0u;  // masked pixel: as invalid
+      const int h = j & 1, zz = j >> 1;
+      const long long Cz = (c0[2] + (h ? SY4[2] : 0ll) + zz * SZ[2]) >> 20;
+      float x = 0.0f;
+      bool band = false;
+      const bool ok = pix >= 0 && voxel_value(raw, Cz, p, &x, &band);
+      sx[j][lane] = x;
+      if (band) spx[j][lane] = pix | (int)0x80000000;
+      passbits |= ok ? (1u << j) : 0u;
+    }
+    if (!__any_sync(0xffffffffu, passbits != 0)) continue;
+    // 3) pool index: from the prefetched bucket, else probe/insert by lane 0
+    const unsigned found = __ballot_sync(0xffffffffu, lane < kSlots && e != kEmpty && (e >> 22) == key);
+    int pool;
+    bool fresh = false;
+    if (found) {
+      pool = (int)(__shfl_sync(0xffffffffu, e, __ffs(found) - 1) & 0x3FFFFFull);
+    } else {
+      int pl = -1, nw = 0;
+      if (lane == 0) {
+        bool is_new;
+        pl = hash_insert(v, b.x, b.y, b.z, &is_new);
+        nw = is_new;
+      }
+      pool = __shfl_sync(0xffffffffu, pl, 0);
+      fresh = __shfl_sync(0xffffffffu, nw, 0) != 0;
+    }
     if (pool < 0) continue;
-    const bool fresh = s_new != 0;
-    uint2* vb = v.vox + (size_t)pool * kBV;
-    uint8_t* wb = v.W + (size_t)pool * kBV;
-#pragma unroll
-    for (int j = 0; j < kVPT; ++j) {
-      const int li = threadIdx.x + j * kIntegThreads;
+    my_new += (lane == 0 && fresh) ? 1u : 0u;
+    my_updated += __popc(passbits);
+    uint2* vb = v.vox + (size_t)pool * kBV + lane;
+    uint8_t* wb = v.W + (size_t)pool * kBV + lane;
+    // 4) read-modify-write
+#pragma unroll 4
+    for (int j = 0; j < kVPL; ++j) {
+      const bool pass = (passbits >> j) & 1u;
       uint2 w;
       unsigned W;
       if (fresh) {
         w = make_uint2(nan_bits, 0u);
         W = 0;
       } else {
-        if (!pass[j]) continue;
-        w = vb[li];
-        W = wb[li];
+        if (!pass) continue;
+        w = vb[32 * j];
+        W = wb[32 * j];
       }
-      if (pass[j]) {
+      if (pass) {
         const float F = __uint_as_float(w.x);
-        const float x = ob[j].x;
-        const float Fn = (W == 0) ? x : ((float)W * F + x) / (float)(W + 1);
+        const float x = sx[j][lane];
+        const int px = spx[j][lane];
+        const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
         w.x = __float_as_uint(Fn);
-        if (ob[j].band) {
-          const uint8_t* c = f.rgb + 3 * (size_t)ob[j].pix;
+        if (px < 0) {  // inside the band: colour too
+          const uint8_t* c = f.rgb + 3 * (size_t)(px & 0x7fffffff);
           const unsigned wc = w.y >> 24;
+          const unsigned den = 2 * (wc + 1);
+          const float rden = __frcp_rn((float)den);
           unsigned out = 0;
 #pragma unroll
           for (int ch = 0; ch < 3; ++ch) {
-            const unsigned num = wc * ((w.y >> (8 * ch)) & 255u) + __ldg(c + ch);
-            out |= ((2 * num + wc + 1) / (2 * (wc + 1))) << (8 * ch);
+            // round half up of (wc C + c) / (wc + 1): exact integer quotient
+            // from a float reciprocal, corrected by one step either way
+            const unsigned num = 2 * (wc * ((w.y >> (8 * ch)) & 255u) + __ldg(c + ch)) + wc + 1;
+            unsigned q = (unsigned)((float)num * rden);
+            if (q * den > num) q -= 1;
+            else if ((q + 1) * den <= num) q += 1;
+            out |= q << (8 * ch);
           }
           w.y = out | (min(wc + 1, (unsigned)p.w_max) << 24);
         }
         W = min(W + 1, (unsigned)p.w_max);
       }
-      vb[li] = w;
-      wb[li] = (uint8_t)W;
+      vb[32 * j] = w;
+      wb[32 * j] = (uint8_t)W;
     }
   }
   my_updated = __reduce_add_sync(0xffffffffu, my_updated);
-  if ((threadIdx.x & 31) == 0 && my_updated) atomicAdd(&st->updated, (unsigned long long)my_updated);
+  my_new = __reduce_add_sync(0xffffffffu, my_new);
+  if (lane == 0 && my_updated) atomicAdd(&st->updated, (unsigned long long)my_updated);
+  if (lane == 0 && my_new) atomicAdd(&st->new_blocks, (int)my_new);
 }
 
 }  // namespace
@@ -404,7 +497,7 @@ rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, c
   k_cull<<<vol->sm_count * 8, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
                                             vol->p.max_candidates, vol->d_status);
   prof_record(vol, EV_KERNEL0, st);
-  k_integrate<<<vol->sm_count * 4, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ, vol->d_cand,
+  k_integrate<<<vol->sm_count * 16, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ, vol->d_cand,
                                                            vol->p.max_candidates);
   prof_record(vol, EV_KERNEL1, st);
   return check_cuda(vol, cudaGetLastError(), "integrate launch");

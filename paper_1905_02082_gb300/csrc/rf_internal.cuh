@@ -56,6 +56,7 @@ struct DevVol {
 // Per-volume constants derived from rf_params.
 struct DevParams {
   float voxel, inv_voxel, tau, w_c, gamma_tau2;
+  float gamma_tau2_f;  // (float)((gamma * tau) * tau), the mask threshold of Eq. 5 in float
   float inv_depth_scale, z_near, d_max;
   double voxel_d, tau_d, gamma_d, depth_scale_d;
   long long v_um, du_um, dmin_um, dmax_um, znear_tick, dmax_tick, tau_tick;
@@ -71,21 +72,11 @@ struct DevFrame {
   float fx, fy, cx, cy, ifx, ify;
   double fxd, fyd, cxd, cyd;
   long long fxq, fyq, cxq, cyq;
+  // float pixel estimates closer than this to a rounding boundary are decided
+  // by the exact integer path (4x the bound on the estimate's error)
+  float amb_u, amb_v;
   const uint16_t* depth;
   const uint8_t* rgb;
-};
-
-// Levenberg-Marquardt state of one registration, resident on the device.
-struct LMState {
-  double T[16];   // accepted pose
-  double Tc[16];  // candidate pose under evaluation
-  float Rf[12];   // float copy of T   (R row-major 3x3, then t)
-  float Rcf[12];  // float copy of Tc
-  double H[21], g[6], E;
-  long long N;
-  double lambda;
-  int done;
-  rf_track_info info;
 };
 
 // Quantised pose and the frustum search region of one integration.
@@ -179,7 +170,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
           atomicOr(status, ST_BARRIER);
           break;
         }
-        __nanosleep(64);
+        if (spins > 4096) __nanosleep(64);  // spin first: most waits are short
       }
     }
     __threadfence();
@@ -187,6 +178,38 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Lighter grid barrier for kernels that synchronise many times: one counter
+// that only grows (zeroed before the launch); the k-th barrier waits until it
+// reaches k * nblocks.  Arrival is a fence plus one atomic add, waiting is an
+// acquire load.  Bounded like grid_barrier.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool grid_sync_counter(unsigned* count, unsigned target, unsigned* status) {
+  __shared__ int s_ok2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    int ok = 1;
+    long long spins = 0;
+    while (ld_acquire_gpu(count) < target) {
+      if (++spins > (1ll << 24)) {
+        ok = 0;
+        atomicOr(status, ST_BARRIER);
+        break;
+      }
+      if (spins > 4096) __nanosleep(64);
+    }
+    s_ok2 = ok;
+  }
+  __syncthreads();
+  return s_ok2 != 0;
 }
 
 }  // namespace rf

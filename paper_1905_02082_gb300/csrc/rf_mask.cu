@@ -32,6 +32,18 @@ __device__ __forceinline__ double lerp_rn(double a, double b, double t) {
 // Fetches the 8 corner SDF values of the cell with lattice origin k; false if
 // any corner is missing or unobserved.
 __device__ __forceinline__ bool corners_of(const DevVol& v, int kx, int ky, int kz, float F[8]) {
+  if ((kx & 7) < 7 && (ky & 7) < 7 && (kz & 7) < 7) {  // all 8 corners in one block
+    const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
+    if (pool < 0) return false;
+    const uint2* base = v.vox + (size_t)pool * kBV + (kx & 7) + 8 * (ky & 7) + 64 * (kz & 7);
+    const int off[8] = {0, 1, 8, 9, 64, 65, 72, 73};
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      F[n] = __uint_as_float(__ldg(&base[off[n]].x));
+      if (F[n] != F[n]) return false;
+    }
+    return true;
+  }
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
     const int x = kx + (n & 1), y = ky + ((n >> 1) & 1), z = kz + ((n >> 2) & 1);
@@ -75,21 +87,25 @@ __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevPar
 
 __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p, const double* __restrict__ T,
                                                uint8_t* __restrict__ seeds, unsigned* guard_count) {
+  // pose and threshold converted once per CTA (conversions use the FP64 pipe)
+  __shared__ float sR[12];
+  __shared__ double s_t64;
+  if (threadIdx.x < 12) {
+    const int i = threadIdx.x < 9 ? threadIdx.x / 3 : threadIdx.x - 9;
+    const int j = threadIdx.x < 9 ? threadIdx.x % 3 : 3;
+    sR[threadIdx.x] = (float)T[i * 4 + j];
+  }
+  if (threadIdx.x == 12) s_t64 = __dmul_rn(__dmul_rn(p.gamma_d, p.tau_d), p.tau_d);
+  __syncthreads();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= f.H * f.W) return;
   const int u = idx % f.W, vv = idx / f.W;
   const unsigned raw = __ldg(f.depth + idx);
   uint8_t seed = 0;
   if (pixel_valid(p, raw)) {
-    const double t64 = __dmul_rn(__dmul_rn(p.gamma_d, p.tau_d), p.tau_d);
-    const float t = (float)t64;
-    float Rf[12];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Rf[i * 3 + j] = (float)T[i * 4 + j];
-      Rf[9 + i] = (float)T[i * 4 + 3];
-    }
+    const double t64 = s_t64;
+    const float t = p.gamma_tau2_f;
+    const float* Rf = sR;
     const float D = (float)raw * p.inv_depth_scale;
     const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
     float q[3], fr[3];

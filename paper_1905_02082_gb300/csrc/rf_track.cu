@@ -3,29 +3,32 @@
 //                         + w_c sum_i (V_I(exp(xi) T x_i) - I(p_i))^2,
 // over three pixel sub-samplings (strides), coarse to fine.
 //
-// One LM iteration is two launches with no host round trip:
-//   k_track_accum  one thread per sampled pixel: Eq. 1 back-projection, rigid
-//                  transform, hash lookup of the 8 lattice corners, trilinear
-//                  SDF and intensity with analytic gradients, residuals and
-//                  Jacobians J = dV/dp [I | -[p]x] (left perturbation), and a
-//                  warp-shuffle + shared-memory reduction of the 21 entries of
-//                  J^T J, the 6 of J^T r, the cost and the valid count into one
-//                  per-CTA partial (FP32);
-//   k_lm_update    one CTA: fixed-order FP64 reduction of the partials, accept or
-//                  reject the candidate (mean cost E/N must decrease), lambda
-//                  update, 6x6 Cholesky of H + lambda diag(H) in FP64, se(3)
-//                  exponential and composition of the next candidate pose.
-// A device flag ends a level early (step below the thresholds); the remaining
-// launches of the level return at once.  Results are deterministic: fixed
-// grids, fixed pixel-to-thread mapping and fixed reduction order.
+// A whole registration (three levels, every LM iteration) is ONE cooperative
+// launch of k_register, one CTA of 512 threads per SM.  Per cost evaluation:
+//   1. every thread takes sampled pixels: Eq. 1 back-projection, rigid
+//      transform, hash lookup of the 8 lattice corners, trilinear SDF and
+//      intensity with analytic gradients, residuals and Jacobians
+//      J = dV/dp [I | -[p]x] (left perturbation);
+//   2. a warp-shuffle + shared-memory reduction of the 21 entries of J^T J,
+//      the 6 of J^T r, the cost and the valid count gives one FP32 partial
+//      per CTA;
+//   3. a bounded grid barrier;
+//   4. EVERY CTA reduces all partials (FP32, the same fixed order) and runs
+//      the same LM step on its shared-memory copy of the LM state, on one
+//      warp: accept or reject the candidate (mean cost E/N must decrease),
+//      update lambda, solve the damped 6x6 system in FP64 (3x3 block
+//      elimination) and compose the next candidate pose exp(delta) T in FP64.
+//      Identical inputs and code give identical states in all CTAs, so no
+//      broadcast is needed.
+// The LM state never leaves shared memory; a level ends early when the step
+// falls below the thresholds.  Results are deterministic: fixed grid, fixed
+// pixel-to-thread mapping, fixed reduction order.
 #include <cmath>
 
 #include "rf_volume.hpp"
 
 namespace rf {
 namespace {
-
-constexpr int kTrackThreads = 256;
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return a * (1.0f - t) + b * t; }
 
@@ -113,262 +116,421 @@ __device__ __forceinline__ void add_jtj(float* acc, const float J[6], float r, f
   acc[27] += w * r * r;
 }
 
-__global__ void __launch_bounds__(kTrackThreads) k_track_accum(DevVol v, DevFrame f, DevParams p,
-                                                                const uint8_t* __restrict__ mask, int stride, int Ws,
-                                                                int npix, const LMState* __restrict__ lm,
-                                                                int use_current, float* __restrict__ partials) {
-  if (!use_current && *(volatile const int*)&lm->done) return;
-  const float* Tf = use_current ? lm->Rf : lm->Rcf;
-  const float R0 = Tf[0], R1 = Tf[1], R2 = Tf[2], R3 = Tf[3], R4 = Tf[4], R5 = Tf[5], R6 = Tf[6], R7 = Tf[7],
-              R8 = Tf[8], t0 = Tf[9], t1 = Tf[10], t2 = Tf[11];
-  float acc[29];
-#pragma unroll
-  for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
-    const int u = (i % Ws) * stride, vv = (i / Ws) * stride;
-    const int idx = vv * f.W + u;
-    const unsigned raw = __ldg(f.depth + idx);
-    if (!pixel_valid(p, raw)) continue;
-    if (mask && __ldg(mask + idx)) continue;
-    const float D = (float)raw * p.inv_depth_scale;
-    const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
-    const float px = R0 * x + R1 * y + R2 * D + t0;
-    const float py = R3 * x + R4 * y + R5 * D + t1;
-    const float pz = R6 * x + R7 * y + R8 * D + t2;
-    float V, gV[3], I, gI[3];
-    bool colour;
-    if (!model_sample(v, p, px, py, pz, &V, gV, &I, gI, &colour)) continue;
-    const float Jd[6] = {gV[0], gV[1], gV[2], py * gV[2] - pz * gV[1], pz * gV[0] - px * gV[2],
-                         px * gV[1] - py * gV[0]};
-    add_jtj(acc, Jd, V, 1.0f);
-    acc[28] += 1.0f;
-    if (colour) {
-      const uint8_t* c = f.rgb + 3 * (size_t)idx;
-      const unsigned cc = (unsigned)__ldg(c) | ((unsigned)__ldg(c + 1) << 8) | ((unsigned)__ldg(c + 2) << 16);
-      const float rc = I - rgb_intensity(cc);
-      const float Jc[6] = {gI[0], gI[1], gI[2], py * gI[2] - pz * gI[1], pz * gI[0] - px * gI[2],
-                           px * gI[1] - py * gI[0]};
-      add_jtj(acc, Jc, rc, p.w_c);
-    }
-  }
-  // warp-shuffle reduction, then across the CTA's warps in fixed order
-  __shared__ float red[kTrackThreads / 32][29];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < 29; ++i) {
-    float s = acc[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[warp][i] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < 29) {
-    float s = 0.0f;
-#pragma unroll
-    for (int w = 0; w < kTrackThreads / 32; ++w) s += red[w][threadIdx.x];
-    partials[blockIdx.x * kPartialStride + threadIdx.x] = s;
-  }
-}
-
 struct LMConst {
   double lambda0, eps_t, eps_r;
   long long min_valid;
+  int iters[3], strides[3];
 };
 
-__device__ void se3_exp_d(const double xi[6], double T[16]) {
-  const double th2 = xi[3] * xi[3] + xi[4] * xi[4] + xi[5] * xi[5];
-  const double th = sqrt(th2);
-  double A, B, C;
-  if (th < 1e-5) {
-    A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-    B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-    C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
-  } else {
-    double s, c;
-    sincos(th, &s, &c);
-    A = s / th;
-    B = (1.0 - c) / th2;
-    C = (th - s) / (th2 * th);
-  }
-  const double wx = xi[3], wy = xi[4], wz = xi[5];
-  const double K[9] = {0, -wz, wy, wz, 0, -wx, -wy, wx, 0};
-  double K2[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) K2[i * 3 + j] = K[i * 3] * K[j] + K[i * 3 + 1] * K[3 + j] + K[i * 3 + 2] * K[6 + j];
-  for (int i = 0; i < 3; ++i) {
-    double t = 0.0;
-    for (int j = 0; j < 3; ++j) {
-      const double I = (i == j) ? 1.0 : 0.0;
-      T[i * 4 + j] = I + A * K[i * 3 + j] + B * K2[i * 3 + j];
-      t += (I + B * K[i * 3 + j] + C * K2[i * 3 + j]) * xi[j];
+// FP64 reciprocal: FP32 seed refined by two FP64 Newton steps (relative
+// error ~(2^-23)^4, i.e. full double precision), far cheaper than a double
+// division on GB300's FP64 pipe.
+__device__ __forceinline__ double rcp_d(double d) {
+  const float df = (float)d;
+  if (!(fabsf(df) > 1e-36f && fabsf(df) < 1e36f)) return 1.0 / d;
+  double r = (double)__frcp_rn(df);
+  r = fma(fma(-d, r, 1.0), r, r);
+  r = fma(fma(-d, r, 1.0), r, r);
+  return r;
+}
+
+// LM state of one registration, one copy in the shared memory of every CTA,
+// plus the scratch of the warp-cooperative FP64 step.
+struct LMShared {
+  double T[16];   // accepted pose
+  double Tc[16];  // candidate pose under evaluation
+  double H[21], g[6], E;
+  double lambda, fin_E;
+  double red[29];
+  // scratch of the damped 6x6 solve and of the exponential map
+  double A6[36], adjP[9], Pi[9], X[12], Y[12], adjS[9], d[6], coef[3], Ex[12];
+  long long N, fin_N;
+  float redf[29];  // FP32 sums of the partials
+  float Rf[12];    // float copy of T  (R row-major, then t)
+  float Rcf[12];   // float copy of Tc
+  int done, accept, solve_ok;
+  rf_track_info info;
+};
+
+// (row, column) of the 21 upper-triangle entries of H, row-major
+__constant__ unsigned char kUpperRow[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+__constant__ unsigned char kUpperCol[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+// Taylor coefficients in th^2 of A = sin(th)/th, B = (1 - cos th)/th^2 and
+// C = (th - sin th)/th^3, highest power first (th^10 ... th^0)
+__constant__ double kExpCoef[3][6] = {
+    {-1.0 / 39916800.0, 1.0 / 362880.0, -1.0 / 5040.0, 1.0 / 120.0, -1.0 / 6.0, 1.0},
+    {-1.0 / 479001600.0, 1.0 / 3628800.0, -1.0 / 40320.0, 1.0 / 720.0, -1.0 / 24.0, 0.5},
+    {-1.0 / 6227020800.0, 1.0 / 39916800.0, -1.0 / 362880.0, 1.0 / 5040.0, -1.0 / 120.0, 1.0 / 6.0}};
+
+// Cofactor (r, c) of a row-major 3x3 matrix; the adjugate is its transpose.
+__device__ __forceinline__ double cofactor3(const double* a, int r, int c) {
+  const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+  return fma(a[r1 * 3 + c1], a[r2 * 3 + c2], -a[r1 * 3 + c2] * a[r2 * 3 + c1]);
+}
+
+// One LM step, executed by the 32 lanes of one warp.  On GB300 every FP64
+// warp instruction costs the FP64 pipe about the same whatever the number of
+// active lanes, so the work is spread across lanes and the number of FP64
+// instructions on the critical path is kept small (about 70).
+//   mode 0: first evaluation of a level, at T (always taken);
+//   mode 1: evaluation of the candidate Tc, accepted when the mean cost
+//           decreases (En/Nn < E/N, compared as En N < E Nn).
+// Solve of (H + lambda diag H) d = -g in FP64 by 3x3 block elimination over
+// the translation / rotation blocks, A = [P Q; Q^T S]:
+//   P^-1 = adj(P)/det P,  [M | y1] = P^-1 [Q | b1],
+//   [Sc | r2] = [S | b2] - Q^T [M | y1]  (Schur complement),
+//   d2 = adj(Sc) r2 / det Sc,  d1 = y1 - M d2,  with b = -g.
+// Then the next candidate Tc = exp(d) T (FP64), with the se(3) exponential
+// R = I + A K + B K^2, t = (I + B K + C K^2) rho, K = [phi]x, K^2 = phi phi^T - th^2 I.
+__device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const LMConst& c, int lane) {
+  if (lane < 29) S.red[lane] = (double)S.redf[lane];
+  __syncwarp();
+  if (lane == 0) {
+    const double En = S.red[27];
+    const long long Nn = (long long)(S.redf[28] + 0.5f);
+    S.info.evals++;
+    S.info.level_evals[level]++;
+    S.solve_ok = 1;
+    if (mode == 0) {
+      S.accept = 1;
+      S.E = En;
+      S.N = Nn;
+      S.fin_E = En;
+      S.fin_N = Nn;
+      S.done = Nn < c.min_valid ? 1 : 0;
+      S.lambda = c.lambda0;
+    } else if (Nn >= c.min_valid && En * (double)S.N < S.E * (double)Nn) {
+      S.accept = 2;
+      S.E = En;
+      S.N = Nn;
+      S.fin_E = En;
+      S.fin_N = Nn;
+      S.lambda *= 0.1;
+    } else {
+      S.accept = 0;
+      S.lambda *= 10.0;
     }
-    T[i * 4 + 3] = t;
   }
-  T[12] = T[13] = T[14] = 0.0;
-  T[15] = 1.0;
-}
-
-// (H + lambda diag H) d = -g, H given as 21 upper-triangle entries.
-__device__ bool lm_solve_d(const double* H, const double* g, double lambda, double d[6]) {
-  double A[6][6], L[6][6];
-  int n = 0;
-  for (int i = 0; i < 6; ++i)
-    for (int j = i; j < 6; ++j) {
-      A[i][j] = H[n];
-      A[j][i] = H[n];
-      ++n;
-    }
-  for (int i = 0; i < 6; ++i) A[i][i] *= (1.0 + lambda);
-  for (int j = 0; j < 6; ++j) {
-    double s = A[j][j];
-    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-    if (!(s > 0.0) || !isfinite(s)) return false;
-    L[j][j] = sqrt(s);
-    for (int i = j + 1; i < 6; ++i) {
-      double t = A[i][j];
-      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-      L[i][j] = t / L[j][j];
+  __syncwarp();
+  const int acc = S.accept;
+  if (acc) {
+    if (lane < 21) S.H[lane] = S.red[lane];
+    else if (lane < 27) S.g[lane - 21] = S.red[lane];
+    if (acc == 2) {
+      if (lane < 16) S.T[lane] = S.Tc[lane];
+      if (lane < 12) S.Rf[lane] = S.Rcf[lane];
     }
   }
-  double y[6];
-  for (int i = 0; i < 6; ++i) {
-    double s = -g[i];
-    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-    y[i] = s / L[i][i];
+  __syncwarp();
+  if (S.done || last) return;
+  // damped matrix
+  if (lane < 21) {
+    const int i = kUpperRow[lane], j = kUpperCol[lane];
+    const double h = i == j ? S.H[lane] * (1.0 + S.lambda) : S.H[lane];
+    S.A6[i * 6 + j] = h;
+    S.A6[j * 6 + i] = h;
   }
-  for (int i = 5; i >= 0; --i) {
-    double s = y[i];
-    for (int k = i + 1; k < 6; ++k) s -= L[k][i] * d[k];
-    d[i] = s / L[i][i];
-  }
-  return true;
-}
-
-__device__ void to_float(const double* T, float* Tf) {
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) Tf[i * 3 + j] = (float)T[i * 4 + j];
-    Tf[9 + i] = (float)T[i * 4 + 3];
-  }
-}
-
-__global__ void k_track_init(LMState* lm, const double* __restrict__ T_init) {
-  if (threadIdx.x != 0) return;
-  for (int i = 0; i < 16; ++i) {
-    lm->T[i] = T_init[i];
-    lm->Tc[i] = T_init[i];
-  }
-  to_float(lm->T, lm->Rf);
-  to_float(lm->T, lm->Rcf);
-  lm->done = 0;
-  lm->E = 0.0;
-  lm->N = 0;
-  lm->lambda = 0.0;
-  rf_track_info z = {};
-  lm->info = z;
-}
-
-// mode 0: first evaluation of a level (at T, always taken); mode 1: candidate.
-__global__ void __launch_bounds__(256) k_lm_update(LMState* lm, const float* __restrict__ partials, int G, int mode,
-                                                   int level, int last, LMConst c) {
-  if (mode == 1 && *(volatile int*)&lm->done) return;
-  __shared__ double red[29];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int comp = warp; comp < 29; comp += 8) {
-    double s = 0.0;
-    for (int k = lane; k < G; k += 32) s += (double)partials[k * kPartialStride + comp];
+  __syncwarp();
+  const double* A6 = S.A6;
+  // P^-1
+  if (lane < 9) {
+    double P[9];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red[comp] = s;
+    for (int k = 0; k < 9; ++k) P[k] = A6[(k / 3) * 6 + (k % 3)];
+    S.adjP[lane] = cofactor3(P, lane % 3, lane / 3);
+  }
+  __syncwarp();
+  const double detP = fma(A6[0], S.adjP[0], fma(A6[1], S.adjP[3], A6[2] * S.adjP[6]));
+  if (!(detP > 0.0) || !isfinite(detP) || !(A6[0] > 0.0)) {
+    if (lane == 0) S.solve_ok = 0;
+  } else {
+    const double rP = rcp_d(detP);
+    if (lane < 9) S.Pi[lane] = S.adjP[lane] * rP;
+    __syncwarp();
+    // [M | y1] = P^-1 [Q | b1]
+    if (lane < 12) {
+      const int r = lane >> 2, cc = lane & 3;
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v = fma(S.Pi[r * 3 + k], cc < 3 ? A6[k * 6 + 3 + cc] : -S.g[k], v);
+      S.X[lane] = v;
+    }
+    __syncwarp();
+    // [Sc | r2] = [S | b2] - Q^T [M | y1]
+    if (lane < 12) {
+      const int r = lane >> 2, cc = lane & 3;
+      double v = cc < 3 ? A6[(3 + r) * 6 + 3 + cc] : -S.g[3 + r];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v = fma(-A6[k * 6 + 3 + r], S.X[k * 4 + cc], v);
+      S.Y[lane] = v;
+    }
+    __syncwarp();
+    if (lane < 9) {
+      double Sc[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Sc[k] = S.Y[(k / 3) * 4 + (k % 3)];
+      S.adjS[lane] = cofactor3(Sc, lane % 3, lane / 3);
+    }
+    __syncwarp();
+    const double detS = fma(S.Y[0], S.adjS[0], fma(S.Y[1], S.adjS[3], S.Y[2] * S.adjS[6]));
+    if (!(detS > 0.0) || !isfinite(detS) || !(S.Y[0] > 0.0)) {
+      if (lane == 0) S.solve_ok = 0;
+    } else {
+      const double rS = rcp_d(detS);
+      if (lane < 3) {
+        double v = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v = fma(S.adjS[lane * 3 + k], S.Y[k * 4 + 3], v);
+        S.d[3 + lane] = v * rS;
+      }
+      __syncwarp();
+      if (lane < 3) {
+        double v = S.X[lane * 4 + 3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v = fma(-S.X[lane * 4 + k], S.d[3 + k], v);
+        S.d[lane] = v;
+      }
+    }
+  }
+  __syncwarp();
+  const double d0 = S.d[0], d1 = S.d[1], d2 = S.d[2], w0 = S.d[3], w1 = S.d[4], w2 = S.d[5];
+  const double nr2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+  const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
+  if (!S.solve_ok || !isfinite(nr2 + th2)) {
+    if (lane == 0) {
+      S.info.converged[level] = 1;
+      S.done = 1;
+    }
+    __syncwarp();
+    return;
+  }
+  if (nr2 < c.eps_t * c.eps_t && th2 < c.eps_r * c.eps_r) {
+    if (lane == 0) {
+      S.info.converged[level] = 1;
+      S.done = 1;
+    }
+    __syncwarp();
+    return;
+  }
+  // exponential map: coefficients A, B, C on lanes 0, 1, 2
+  if (lane < 3) {
+    double v;
+    if (th2 < 0.01) {
+      v = kExpCoef[lane][0];
+#pragma unroll
+      for (int k = 1; k < 6; ++k) v = fma(v, th2, kExpCoef[lane][k]);
+    } else {
+      const double th = sqrt(th2);
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      v = lane == 0 ? sn / th : (lane == 1 ? (1.0 - cs) / th2 : (th - sn) / (th2 * th));
+    }
+    S.coef[lane] = v;
+  }
+  __syncwarp();
+  // R (lanes 0-8) = I + A K + B K^2 and V (lanes 9-17) = I + B K + C K^2
+  if (lane < 18) {
+    const int e = lane % 9, i = e / 3, j = e % 3;
+    const double w[3] = {w0, w1, w2};
+    const double kij = (i == j) ? 0.0 : ((j == (i + 1) % 3) ? -w[(i + 2) % 3] : w[(i + 1) % 3]);
+    const double k2ij = fma(w[i], w[j], i == j ? -th2 : 0.0);
+    const double a = lane < 9 ? S.coef[0] : S.coef[1], b = lane < 9 ? S.coef[1] : S.coef[2];
+    S.A6[lane] = fma(a, kij, fma(b, k2ij, i == j ? 1.0 : 0.0));  // scratch reuse
+  }
+  __syncwarp();
+  if (lane < 12) {
+    const int i = lane >> 2, j = lane & 3;
+    // Ex = [R | V rho]
+    double v;
+    if (j < 3) {
+      v = S.A6[i * 3 + j];
+    } else {
+      v = fma(S.A6[9 + i * 3], d0, fma(S.A6[9 + i * 3 + 1], d1, S.A6[9 + i * 3 + 2] * d2));
+    }
+    S.Ex[lane] = v;
+  }
+  __syncwarp();
+  // Tc = Ex T  (rows 0-2; the last row stays 0 0 0 1)
+  if (lane < 12) {
+    const int i = lane >> 2, j = lane & 3;
+    double v = j == 3 ? S.Ex[i * 4 + 3] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v = fma(S.Ex[i * 4 + k], S.T[k * 4 + j], v);
+    S.Tc[lane] = v;
+    S.Rcf[j < 3 ? i * 3 + j : 9 + i] = (float)v;
+  }
+  if (lane >= 12 && lane < 16) S.Tc[lane] = lane == 15 ? 1.0 : 0.0;
+  __syncwarp();
+}
+
+constexpr int kRegThreads = 512;
+constexpr int kRegWarps = kRegThreads / 32;
+
+// One whole registration (see the file comment).  partials: 2 x 29 x gridDim
+// floats (double-buffered by evaluation parity); bar: 2 zeroed words.
+__global__ void __launch_bounds__(kRegThreads, 1)
+    k_register(DevVol v, DevFrame f, DevParams p, const uint8_t* __restrict__ mask, const double* __restrict__ T_init,
+               double* __restrict__ T_out, rf_track_info* info_out, LMConst c, float* partials, unsigned* bar,
+               unsigned* status) {
+  __shared__ LMShared S;
+  __shared__ float red[kRegWarps][29];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = gridDim.x;
+  if (threadIdx.x < 16) {
+    S.T[threadIdx.x] = T_init[threadIdx.x];
+    S.Tc[threadIdx.x] = T_init[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    S.done = 0;
+    S.E = 0.0;
+    S.N = 0;
+    S.fin_E = 0.0;
+    S.fin_N = 0;
+    S.lambda = 0.0;
+    rf_track_info z = {};
+    S.info = z;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const double En = red[27];
-  const long long Nn = llrint(red[28]);
-  lm->info.evals++;
-  lm->info.level_evals[level]++;
-  if (mode == 0) {
-    for (int i = 0; i < 21; ++i) lm->H[i] = red[i];
-    for (int i = 0; i < 6; ++i) lm->g[i] = red[21 + i];
-    lm->E = En;
-    lm->N = Nn;
-    lm->info.final_cost = Nn > 0 ? En / (double)Nn : 0.0;
-    lm->info.final_valid = Nn;
-    lm->done = 0;
-    if (Nn < c.min_valid) {
-      lm->done = 1;
-      return;
-    }
-    lm->lambda = c.lambda0;
-  } else {
-    if (Nn >= c.min_valid && En / (double)Nn < lm->E / (double)lm->N) {
-      for (int i = 0; i < 16; ++i) lm->T[i] = lm->Tc[i];
-      for (int i = 0; i < 12; ++i) lm->Rf[i] = lm->Rcf[i];
-      for (int i = 0; i < 21; ++i) lm->H[i] = red[i];
-      for (int i = 0; i < 6; ++i) lm->g[i] = red[21 + i];
-      lm->E = En;
-      lm->N = Nn;
-      lm->lambda /= 10.0;
-      lm->info.final_cost = En / (double)Nn;
-      lm->info.final_valid = Nn;
-    } else {
-      lm->lambda *= 10.0;
-    }
-    if (last) return;
+  if (threadIdx.x < 12) {
+    const int i = threadIdx.x < 9 ? threadIdx.x / 3 : threadIdx.x - 9;
+    const int j = threadIdx.x < 9 ? threadIdx.x % 3 : 3;
+    S.Rf[threadIdx.x] = (float)S.T[i * 4 + j];
+    S.Rcf[threadIdx.x] = S.Rf[threadIdx.x];
   }
-  double d[6];
-  if (!lm_solve_d(lm->H, lm->g, lm->lambda, d)) {
-    lm->info.converged[level] = 1;
-    lm->done = 1;
-    return;
-  }
-  const double nr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-  const double nw = sqrt(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
-  if (nr < c.eps_t && nw < c.eps_r) {
-    lm->info.converged[level] = 1;
-    lm->done = 1;
-    return;
-  }
-  double Ex[16];
-  se3_exp_d(d, Ex);
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      double s = 0.0;
-      for (int k = 0; k < 4; ++k) s += Ex[i * 4 + k] * lm->T[k * 4 + j];
-      lm->Tc[i * 4 + j] = s;
+  __syncthreads();
+  int eval = 0;
+  for (int l = 0; l < 3; ++l) {
+    const int stride = c.strides[l];
+    const int Ws = (f.W + stride - 1) / stride, Hs = (f.H + stride - 1) / stride;
+    const int npix = Ws * Hs;
+    const int iters = c.iters[l];
+    for (int it = 0; it <= iters; ++it) {
+      const int mode = it == 0 ? 0 : 1;
+      if (mode == 1 && S.done) break;  // identical decision in every CTA
+      const float* Tf = mode == 0 ? S.Rf : S.Rcf;
+      const float R0 = Tf[0], R1 = Tf[1], R2 = Tf[2], R3 = Tf[3], R4 = Tf[4], R5 = Tf[5], R6 = Tf[6], R7 = Tf[7],
+                  R8 = Tf[8], t0 = Tf[9], t1 = Tf[10], t2 = Tf[11];
+      float acc[29];
+#pragma unroll
+      for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
+      for (int i = blockIdx.x * kRegThreads + threadIdx.x; i < npix; i += G * kRegThreads) {
+        const int u = (i % Ws) * stride, vv = (i / Ws) * stride;
+        const int idx = vv * f.W + u;
+        const unsigned raw = __ldg(f.depth + idx);
+        if (!pixel_valid(p, raw)) continue;
+        if (mask && __ldg(mask + idx)) continue;
+        const float D = (float)raw * p.inv_depth_scale;
+        const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
+        const float px = R0 * x + R1 * y + R2 * D + t0;
+        const float py = R3 * x + R4 * y + R5 * D + t1;
+        const float pz = R6 * x + R7 * y + R8 * D + t2;
+        float V, gV[3], I, gI[3];
+        bool colour;
+        if (!model_sample(v, p, px, py, pz, &V, gV, &I, gI, &colour)) continue;
+        const float Jd[6] = {gV[0], gV[1], gV[2], py * gV[2] - pz * gV[1], pz * gV[0] - px * gV[2],
+                             px * gV[1] - py * gV[0]};
+        add_jtj(acc, Jd, V, 1.0f);
+        acc[28] += 1.0f;
+        if (colour) {
+          const uint8_t* cp = f.rgb + 3 * (size_t)idx;
+          const unsigned cc = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
+          const float rc = I - rgb_intensity(cc);
+          const float Jc[6] = {gI[0], gI[1], gI[2], py * gI[2] - pz * gI[1], pz * gI[0] - px * gI[2],
+                               px * gI[1] - py * gI[0]};
+          add_jtj(acc, Jc, rc, p.w_c);
+        }
+      }
+      // CTA partial: warp shuffles, then the warps in fixed order
+#pragma unroll
+      for (int i = 0; i < 29; ++i) {
+        float sv = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (lane == 0) red[warp][i] = sv;
+      }
+      __syncthreads();
+      float* part = partials + (size_t)(eval & 1) * 29 * G;
+      if (threadIdx.x < 29) {
+        float sv = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kRegWarps; ++w) sv += red[w][threadIdx.x];
+        part[threadIdx.x * G + blockIdx.x] = sv;
+      }
+      if (!grid_sync_counter(bar, (unsigned)(eval + 1) * (unsigned)G, status)) return;
+      // every CTA: FP64 reduction of all partials (L1 bypassed: written by others)
+      // FP32 reduction in a fixed order: lane-strided sums, then a shuffle tree
+      {
+        // warp w reduces components w and w + 16 (both rows' loads in flight)
+        const int ca = warp, cb = warp + kRegWarps;
+        const float* ra = part + ca * G;
+        const float* rb = part + (cb < 29 ? cb : ca) * G;
+        float fa = 0.0f, fb = 0.0f;
+        for (int k = lane; k < G; k += 32) {
+          fa += __ldcg(ra + k);
+          fb += __ldcg(rb + k);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          fa += __shfl_down_sync(0xffffffffu, fa, o);
+          fb += __shfl_down_sync(0xffffffffu, fb, o);
+        }
+        if (lane == 0) {
+          S.redf[ca] = fa;
+          if (cb < 29) S.redf[cb] = fb;
+        }
+      }
+      __syncthreads();
+      if (warp == 0) lm_step_warp(S, mode, l, it == iters, c, lane);
+      __syncthreads();
+      ++eval;
     }
-  to_float(lm->Tc, lm->Rcf);
-}
-
-__global__ void k_track_final(const LMState* __restrict__ lm, double* T_out, rf_track_info* info) {
-  const int i = threadIdx.x;
-  if (i < 16) T_out[i] = lm->T[i];
-  if (i == 0 && info) *info = lm->info;
+  }
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < 16) T_out[threadIdx.x] = S.T[threadIdx.x];
+    if (threadIdx.x == 0 && info_out) {
+      rf_track_info out = S.info;
+      out.final_cost = S.fin_N > 0 ? S.fin_E / (double)S.fin_N : 0.0;
+      out.final_valid = S.fin_N;
+      *info_out = out;
+    }
+  }
 }
 
 }  // namespace
 
+int register_max_grid(int device) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_register, kRegThreads, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return per_sm * sms;
+}
+
 rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
                        rf_track_info* info, cudaStream_t st) {
-  LMConst c{vol->p.lm_lambda0, vol->p.lm_eps_trans, vol->p.lm_eps_rot, (long long)vol->p.lm_min_valid};
-  k_track_init<<<1, 32, 0, st>>>(vol->d_lm, T_init);
+  LMConst c;
+  c.lambda0 = vol->p.lm_lambda0;
+  c.eps_t = vol->p.lm_eps_trans;
+  c.eps_r = vol->p.lm_eps_rot;
+  c.min_valid = vol->p.lm_min_valid;
   for (int l = 0; l < 3; ++l) {
-    const int s = vol->p.lm_strides[l];
-    const int Ws = (f.W + s - 1) / s, Hs = (f.H + s - 1) / s;
-    const int npix = Ws * Hs;
-    int G = (npix + kTrackThreads - 1) / kTrackThreads;
-    G = G < 1 ? 1 : (G > vol->max_partials ? vol->max_partials : G);
-    const int iters = vol->p.lm_iters[l];
-    k_track_accum<<<G, kTrackThreads, 0, st>>>(vol->dv, f, vol->dp, mask, s, Ws, npix, vol->d_lm, 1,
-                                               vol->d_partials);
-    k_lm_update<<<1, 256, 0, st>>>(vol->d_lm, vol->d_partials, G, 0, l, iters == 0, c);
-    for (int it = 0; it < iters; ++it) {
-      k_track_accum<<<G, kTrackThreads, 0, st>>>(vol->dv, f, vol->dp, mask, s, Ws, npix, vol->d_lm, 0,
-                                                 vol->d_partials);
-      k_lm_update<<<1, 256, 0, st>>>(vol->d_lm, vol->d_partials, G, 1, l, it == iters - 1, c);
-    }
+    c.iters[l] = vol->p.lm_iters[l];
+    c.strides[l] = vol->p.lm_strides[l];
   }
-  k_track_final<<<1, 32, 0, st>>>(vol->d_lm, T_out, info);
-  return check_cuda(vol, cudaGetLastError(), "track launch");
+  rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_regbar, 0, 2 * sizeof(unsigned), st), "barrier reset");
+  if (s != RF_OK) return s;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(vol->reg_grid);
+  cfg.blockDim = dim3(kRegThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return check_cuda(vol,
+                    cudaLaunchKernelEx(&cfg, k_register, vol->dv, f, vol->dp, mask, T_init, T_out, info, c,
+                                       vol->d_partials, vol->d_regbar, vol->d_status),
+                    "registration launch");
 }
 
 }  // namespace rf

@@ -32,9 +32,9 @@ struct rf_volume {
   unsigned* d_status = nullptr;
 
   // registration scratch
-  rf::LMState* d_lm = nullptr;
-  float* d_partials = nullptr;
-  int max_partials = 0;
+  float* d_partials = nullptr;  // 2 x 29 x reg_grid floats (also the mesh counter)
+  unsigned* d_regbar = nullptr;  // grid-barrier words of the registration kernel
+  int reg_grid = 0;
 
   // mask scratch
   uint8_t* d_seeds = nullptr;
