@@ -19,6 +19,7 @@ to frames/s of the full frame.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import multiprocessing as mp
 import os
@@ -93,6 +94,30 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+FLOPS_PER_SAMPLE = 320  # FP32 flops of one sampled pixel in one cost evaluation (depth + colour terms)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank is an independent camera stream: its own seeded sequence."""
+    return 1000 + rank
+
+
+def max_over_ranks(value_ms: float, dist, device) -> float:
+    """The timed region of the slowest rank (the whole job's time)."""
+    if dist is None:
+        return value_ms
+    import torch
+    t = torch.tensor([value_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, timed_ms: float) -> float:
+    """Frames of all ranks divided by the slowest rank's timed region."""
+    return world * steps / (timed_ms / 1000.0)
 
 
 def measured_peaks():
@@ -190,7 +215,7 @@ def main():
 
     n_frames = args.warmup + args.steps
     workers = min(16, os.cpu_count() or 1)
-    frames = make_frames(seed=rank, n=n_frames, workers=workers)
+    frames = make_frames(seed=rank_seed(rank), n=n_frames, workers=workers)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -227,7 +252,8 @@ def main():
     vol.sync()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    profs = []
+    profs, infos = [], []
+    info_dev = torch.zeros(ctypes.sizeof(R.rf_track_info), dtype=torch.uint8, device=dev)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -238,10 +264,11 @@ def main():
         flush.zero_()  # L2 flush between steps, outside the step's events
         fr = vol.frame(d_depth[i], d_rgb[i], K)
         ev[k][0].record(stream)
-        R.rf_process_frame(vol.h, fr, T, Tn, mask, None, stream)
+        R.rf_process_frame(vol.h, fr, T, Tn, mask, info_dev, stream)
         ev[k][1].record(stream)
         T, Tn = Tn, T
         profs.append(vol.profile(stream))  # synchronises; reads this frame's events
+        infos.append(R.Volume.info_of(info_dev))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -249,20 +276,28 @@ def main():
         dist.barrier()
     vol.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    timed_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([timed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        timed_ms = float(t.item())
-    value = world * args.steps / (timed_ms / 1000.0)
+    timed_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = job_throughput(world, args.steps, timed_ms)
 
-    # dominant kernel: per-voxel integration update (the largest byte mover)
     peak, peak_kind = measured_peaks()
+    # integration kernel (the HBM byte mover): 18 B per updated voxel, 4.5 KB per new block
     kern_ms = [p.integrate_kernel_ms for p in profs]
     upd = [p.updated_voxels for p in profs]
     newb = [p.new_blocks for p in profs]
     bytes_per = [18 * u + 9 * 512 * nb for u, nb in zip(upd, newb)]
     ach = (sum(bytes_per) / len(bytes_per)) / (sum(kern_ms) / len(kern_ms) / 1000.0) / 1e9
+    # registration kernel (the dominant kernel by time): FP32 algorithmic flops,
+    # FLOPS_PER_SAMPLE per sampled pixel and cost evaluation, against the
+    # CUDA-core FP32 peak (152 SMs x 128 lanes x 2 flops x 2.07 GHz)
+    p = vol.params
+    npix = [((cam.width + p.lm_strides[l] - 1) // p.lm_strides[l]) * ((cam.height + p.lm_strides[l] - 1) //
+                                                                          p.lm_strides[l]) for l in range(3)]
+    reg_ms = [pr.track_ms[1] for pr in profs]  # the second registration (its info is returned)
+    reg_flops = [FLOPS_PER_SAMPLE * sum(inf.level_evals[l] * npix[l] for l in range(3)) for inf in infos]
+    reg_tflops = (sum(reg_flops) / len(reg_flops)) / (sum(reg_ms) / len(reg_ms) / 1000.0) / 1e12
+    # whole frame: algorithmic bytes (inputs + integration + model read by tracking) over the frame time
+    frame_bytes = [b + cam.width * cam.height * 5 for b in bytes_per]
+    frame_gbs = (sum(frame_bytes) / len(frame_bytes)) / (statistics.mean(step_ms) / 1000.0) / 1e9
     stage = {k: statistics.mean(getattr(p, k) if k != "track_ms" else p.track_ms[0] + p.track_ms[1] for p in profs)
              for k in ("frame_ms", "track_ms", "mask_ms", "integrate_ms", "integrate_kernel_ms")}
 
@@ -293,12 +328,10 @@ def main():
                "steps": n_e2e, "api": "rf_process_frame_host"}
         vol2.close()
 
-    # kernels of this library per whole frame (graph nodes): per registration one
-    # init, one final, and per level (1 + iters) accumulation + LM-step pairs;
-    # mask: seeds, erosion, flood fill, dilation; integration: 5 kernels
-    p = vol.params
-    per_reg = 2 + sum(2 * (1 + p.lm_iters[l]) for l in range(3))
-    launches_per_frame = 2 * per_reg + 4 + 5
+    # kernels of this library per whole frame (graph nodes): one cooperative
+    # launch per registration (2), mask: seeds, erosion, flood fill,
+    # dilation (4), integration: prep, tile maxima, frustum, cull, update (5)
+    launches_per_frame = 2 + 4 + 5
     if rank == 0:
         st = vol.stats()
         line = {
@@ -312,10 +345,18 @@ def main():
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "mean": statistics.mean(step_ms)},
             "stages_ms": stage,
-            "roofline": {"bound": "hbm", "kernel": "k_integrate (per-voxel TSDF/colour update)", "achieved": ach,
-                         "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                         "peak_source": peak_kind,
-                         "bytes_per_launch": statistics.mean(bytes_per), "launch_ms": statistics.mean(kern_ms)},
+            "roofline": {"bound": "alu", "kernel": "k_register (one registration: 3 levels, all LM evaluations)",
+                         "achieved": reg_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": reg_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                         "flops_per_launch": statistics.mean(reg_flops), "launch_ms": statistics.mean(reg_ms),
+                         "note": "latency-bound: dependent LM chain with a grid barrier per evaluation"},
+            "roofline_integrate": {"bound": "hbm", "kernel": "k_integrate (per-voxel TSDF/colour update)",
+                                   "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                   "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
+                                   "bytes_per_launch": statistics.mean(bytes_per),
+                                   "launch_ms": statistics.mean(kern_ms)},
+            "frame_hbm": {"achieved": frame_gbs, "peak": peak, "unit": "GB/s", "frac": frame_gbs / peak},
             "work": {"updated_voxels": statistics.mean(upd), "new_blocks": statistics.mean(newb),
                      "candidates": statistics.mean(p.candidates for p in profs), "blocks": st.n_blocks,
                      "guard_pixels": statistics.mean(p.guard_pixels for p in profs)},
