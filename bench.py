@@ -330,8 +330,9 @@ def main():
 
     # kernels of this library per whole frame (graph nodes): one cooperative
     # launch per registration (2), mask: seeds, erosion, flood fill,
-    # dilation (4), integration: prep, tile maxima, frustum, cull, update (5)
-    launches_per_frame = 2 + 4 + 5
+    # dilation (4), integration: prep, tile maxima, frustum, cull, update,
+    # neighbour tables (6)
+    launches_per_frame = 2 + 4 + 6
     if rank == 0:
         st = vol.stats()
         line = {

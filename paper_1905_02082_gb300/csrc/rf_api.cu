@@ -158,7 +158,7 @@ __global__ void k_import(DevVol v, const int4* __restrict__ coords, int n, int b
     return;
   }
   const unsigned long long key = pack_key(c.x, c.y, c.z);
-  const unsigned long long b = mix64(key) & v.bucket_mask;
+  const unsigned long long b = bucket_of(key, v.bucket_mask);
   for (int pr = 0; pr < kMaxProbe; ++pr) {
     unsigned long long* bp = v.hash + ((b + pr) & v.bucket_mask) * kSlots;
     for (int s = 0; s < kSlots; ++s) {
@@ -333,7 +333,7 @@ rf_status rf_destroy_volume(rf_volume* vol) {
   for (auto& g : vol->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& e : vol->ev)
     if (e) cudaEventDestroy(e);
-  void* dev[] = {vol->d_hash, vol->d_vox,  vol->d_W,       vol->d_coords, vol->d_nblocks, vol->d_status,
+  void* dev[] = {vol->d_hash, vol->d_vox,  vol->d_W,       vol->d_coords, vol->d_nbr, vol->d_nblocks, vol->d_status,
                  vol->d_regbar, vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
                  vol->d_tilemax, vol->d_cand, vol->d_depth, vol->d_rgb,   vol->d_mask,    vol->d_T, vol->d_info,
                  vol->d_guard};
@@ -381,7 +381,8 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
   const size_t nslots = (size_t)n_buckets * kSlots;
   if ((s = dalloc(vol, &vol->d_hash, nslots, "hash")) || (s = dalloc(vol, &vol->d_vox, (size_t)max_blocks * kBV, "voxels")) ||
       (s = dalloc(vol, &vol->d_W, (size_t)max_blocks * kBV, "weights")) ||
-      (s = dalloc(vol, &vol->d_coords, (size_t)max_blocks, "coords")) || (s = dalloc(vol, &vol->d_nblocks, 1, "pool")) ||
+      (s = dalloc(vol, &vol->d_coords, (size_t)max_blocks, "coords")) ||
+      (s = dalloc(vol, &vol->d_nbr, 2 * (size_t)max_blocks, "neighbour tables")) || (s = dalloc(vol, &vol->d_nblocks, 1, "pool")) ||
       (s = dalloc(vol, &vol->d_status, 1, "status")) || (s = dalloc(vol, &vol->d_regbar, 2, "barrier")) ||
       (s = dalloc(vol, &vol->d_partials, (size_t)2 * 29 * vol->reg_grid + 2, "partials")) ||
       (s = dalloc(vol, &vol->d_seeds, npix, "seeds")) || (s = dalloc(vol, &vol->d_md, npix, "mask work")) ||
@@ -400,6 +401,7 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
   vol->dv.vox = vol->d_vox;
   vol->dv.W = vol->d_W;
   vol->dv.coords = vol->d_coords;
+  vol->dv.nbr = vol->d_nbr;
   vol->dv.n_blocks = vol->d_nblocks;
   vol->dv.max_blocks = (int)max_blocks;
   vol->dv.status = vol->d_status;
@@ -620,6 +622,8 @@ rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coor
   }
   int nb = (int)n_blocks;
   if (!s) s = check_cuda(vol, cudaMemcpy(vol->d_nblocks, &nb, sizeof(int), cudaMemcpyHostToDevice), "import count");
+  if (!s) s = launch_nbr_fixup(vol, nullptr, 0, nullptr);
+  if (!s) s = check_cuda(vol, cudaDeviceSynchronize(), "import sync");
   if (s) return s;
   return rf_sync_status(vol, nullptr);
 }

@@ -31,7 +31,7 @@ namespace {
 
 // Quantised pose (one entry per lane: conversions run on the FP64 pipe, so
 // they are spread over lanes) and reset of the per-frame counters.
-__global__ void k_integ_prep(const double* __restrict__ T, IntegState* st) {
+__global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const int* __restrict__ n_blocks) {
   const int a = threadIdx.x;
   if (a < 9) {
     const int i = a / 3, j = a % 3;
@@ -48,6 +48,7 @@ __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st) {
     st->clipped = 0;
     st->new_blocks = 0;
     st->updated = 0ull;
+    st->pool_before = *n_blocks;
   }
 }
 
@@ -289,7 +290,7 @@ __device__ int hash_insert(const DevVol& v, int bx, int by, int bz, bool* is_new
     return -1;
   }
   const unsigned long long key = pack_key(bx, by, bz);
-  const unsigned long long b = mix64(key) & v.bucket_mask;
+  const unsigned long long b = bucket_of(key, v.bucket_mask);
   int pool = -1;
   for (int pr = 0; pr < kMaxProbe; ++pr) {
     unsigned long long* bp = v.hash + ((b + pr) & v.bucket_mask) * kSlots;
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame 
     const int4 b = cand[ci];
     const unsigned long long key = pack_key(b.x, b.y, b.z);
     const bool in_range = coord_ok(b.x, b.y, b.z);
-    const unsigned long long bucket = mix64(key) & v.bucket_mask;
+    const unsigned long long bucket = bucket_of(key, v.bucket_mask);
     unsigned long long e = kEmpty;
     if (lane < kSlots && in_range) e = __ldcg(v.hash + bucket * kSlots + lane);  // prefetch
     // exact camera coordinates of voxel (lane & 7, lane >> 3, 0) of this block
@@ -487,11 +488,41 @@ __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame 
   if (lane == 0 && my_new) atomicAdd(&st->new_blocks, (int)my_new);
 }
 
+// Neighbour tables of the blocks allocated since `lo`: each new block gets
+// the pools of its 7 positive neighbours, and each existing negative
+// neighbour gets the new block in the matching slot.  Runs after the
+// integration (the hash is complete and read-only here).
+__global__ void __launch_bounds__(256) k_nbr_fixup(DevVol v, const int* __restrict__ lo_ptr, int lo_value) {
+  const int lo = lo_ptr ? *lo_ptr : lo_value;
+  const int hi = min(*(volatile int*)v.n_blocks, v.max_blocks);
+  int* flat = reinterpret_cast<int*>(v.nbr);
+  for (int b = lo + blockIdx.x * blockDim.x + threadIdx.x; b < hi; b += gridDim.x * blockDim.x) {
+    const int4 c = v.coords[b];
+    if (c.w == 0) continue;
+    int t[8];
+    t[0] = b;
+#pragma unroll
+    for (int o = 1; o < 8; ++o) t[o] = hash_find(v, c.x + (o & 1), c.y + ((o >> 1) & 1), c.z + ((o >> 2) & 1));
+    v.nbr[2 * (size_t)b] = make_int4(t[0], t[1], t[2], t[3]);
+    v.nbr[2 * (size_t)b + 1] = make_int4(t[4], t[5], t[6], t[7]);
+#pragma unroll
+    for (int o = 1; o < 8; ++o) {
+      const int n = hash_find(v, c.x - (o & 1), c.y - ((o >> 1) & 1), c.z - ((o >> 2) & 1));
+      if (n >= 0) flat[8 * (size_t)n + o] = b;
+    }
+  }
+}
+
 }  // namespace
+
+rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st) {
+  k_nbr_fixup<<<vol->sm_count * 2, 256, 0, st>>>(vol->dv, lo_ptr, lo);
+  return check_cuda(vol, cudaGetLastError(), "neighbour table launch");
+}
 
 rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st) {
   const int tiles_x = (f.W + kTile - 1) / kTile, tiles_y = (f.H + kTile - 1) / kTile;
-  k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ);
+  k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks);
   k_tilemax<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x);
   k_integ_aabb<<<1, 32, 0, st>>>(T, f, vol->dp, vol->d_integ);
   k_cull<<<vol->sm_count * 8, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
@@ -500,7 +531,9 @@ rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, c
   k_integrate<<<vol->sm_count * 16, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ, vol->d_cand,
                                                            vol->p.max_candidates);
   prof_record(vol, EV_KERNEL1, st);
-  return check_cuda(vol, cudaGetLastError(), "integrate launch");
+  rf_status s = check_cuda(vol, cudaGetLastError(), "integrate launch");
+  if (s != RF_OK) return s;
+  return launch_nbr_fixup(vol, &vol->d_integ->pool_before, 0, st);
 }
 
 }  // namespace rf

@@ -48,6 +48,8 @@ struct DevVol {
   uint2* vox;
   uint8_t* W;
   int4* coords;  // block coordinate per pool index
+  int4* nbr;     // per pool index, 2 x int4: pools of the blocks at offset (dx,dy,dz) in {0,1}^3,
+                 // slot dx + 2 dy + 4 dz (slot 0 = itself), -1 where absent
   int* n_blocks;
   int max_blocks;
   unsigned* status;
@@ -93,6 +95,7 @@ struct IntegState {
   int n_cand;
   int work;
   int new_blocks;
+  int pool_before;  // pool size when the integration started (new blocks follow it)
   unsigned long long updated;
 };
 
@@ -106,21 +109,23 @@ __device__ __forceinline__ unsigned long long pack_key(int bx, int by, int bz) {
          (unsigned long long)(bz & 0x3FFF);
 }
 
-// splitmix64 finaliser as the bucket hash
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z ^= z >> 30;
-  z *= 0xbf58476d1ce4e5b9ull;
-  z ^= z >> 27;
-  z *= 0x94d049bb133111ebull;
-  z ^= z >> 31;
-  return z;
+// Bucket of a packed block key: murmur3's 32-bit finaliser applied to the
+// two halves of the key folded together (32-bit integer ops only).
+__device__ __forceinline__ unsigned long long bucket_of(unsigned long long key, unsigned long long mask) {
+  unsigned k = (unsigned)key ^ ((unsigned)(key >> 32) * 0x9E3779B9u);
+  k ^= k >> 16;
+  k *= 0x85EBCA6Bu;
+  k ^= k >> 13;
+  k *= 0xC2B2AE35u;
+  k ^= k >> 16;
+  return (unsigned long long)k & mask;
 }
 
 // Read-only lookup for kernels that do not insert (tracking, mask, mesh).
 __device__ __forceinline__ int hash_find(const DevVol& v, int bx, int by, int bz) {
   if (!coord_ok(bx, by, bz)) return -1;
   const unsigned long long key = pack_key(bx, by, bz);
-  unsigned long long b = mix64(key) & v.bucket_mask;
+  const unsigned long long b = bucket_of(key, v.bucket_mask);
   for (int p = 0; p < kMaxProbe; ++p) {
     const ulonglong2* bp = reinterpret_cast<const ulonglong2*>(v.hash + ((b + p) & v.bucket_mask) * kSlots);
     const ulonglong2 e01 = __ldg(bp);
@@ -135,10 +140,13 @@ __device__ __forceinline__ int hash_find(const DevVol& v, int bx, int by, int bz
   return -1;
 }
 
-__device__ __forceinline__ float rgb_intensity(unsigned c) {
-  // Sec. III-B: I = 0.2126 R + 0.7152 G + 0.0722 B, scaled to [0, 1]
-  return (0.2126f * (float)(c & 255u) + 0.7152f * (float)((c >> 8) & 255u) + 0.0722f * (float)((c >> 16) & 255u)) *
-         (1.0f / 255.0f);
+
+// 2126 R + 7152 G + 722 B as a float: the intensity of Sec. III-B times
+// 255e4 (exact integer arithmetic, one conversion).
+constexpr float kIntensityScale = 1.0f / 2550000.0f;
+__device__ __forceinline__ float rgb_intensity_raw(unsigned c) {
+  const int s = 2126 * (int)(c & 255u) + 7152 * (int)((c >> 8) & 255u) + 722 * (int)((c >> 16) & 255u);
+  return (float)s;
 }
 
 __device__ __forceinline__ bool pixel_valid(const DevParams& p, unsigned raw) {
@@ -231,4 +239,6 @@ enum ProfEvent { EV_FRAME0, EV_TRACK1_END, EV_MASK_END, EV_TRACK2_END, EV_INTEG0
                  EV_COUNT };
 void prof_record(rf_volume* vol, int ev, cudaStream_t st);
 rf_status run_mesh(rf_volume* vol, float* verts, uint8_t* colors, int64_t cap, int64_t* n, cudaStream_t st);
+// neighbour tables of the blocks allocated since *lo_ptr (or since lo when lo_ptr is null)
+rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st);
 }  // namespace rf

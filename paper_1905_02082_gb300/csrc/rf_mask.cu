@@ -32,10 +32,11 @@ __device__ __forceinline__ double lerp_rn(double a, double b, double t) {
 // Fetches the 8 corner SDF values of the cell with lattice origin k; false if
 // any corner is missing or unobserved.
 __device__ __forceinline__ bool corners_of(const DevVol& v, int kx, int ky, int kz, float F[8]) {
-  if ((kx & 7) < 7 && (ky & 7) < 7 && (kz & 7) < 7) {  // all 8 corners in one block
-    const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
-    if (pool < 0) return false;
-    const uint2* base = v.vox + (size_t)pool * kBV + (kx & 7) + 8 * (ky & 7) + 64 * (kz & 7);
+  const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
+  if (pool < 0) return false;
+  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
+  if (lx < 7 && ly < 7 && lz < 7) {  // all 8 corners in one block
+    const uint2* base = v.vox + (size_t)pool * kBV + lx + 8 * ly + 64 * lz;
     const int off[8] = {0, 1, 8, 9, 64, 65, 72, 73};
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
@@ -44,12 +45,14 @@ __device__ __forceinline__ bool corners_of(const DevVol& v, int kx, int ky, int 
     }
     return true;
   }
+  const int4 n0 = __ldg(v.nbr + 2 * (size_t)pool), n1 = __ldg(v.nbr + 2 * (size_t)pool + 1);
+  const int nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
-    const int x = kx + (n & 1), y = ky + ((n >> 1) & 1), z = kz + ((n >> 2) & 1);
-    const int pool = hash_find(v, x >> 3, y >> 3, z >> 3);
-    if (pool < 0) return false;
-    F[n] = __uint_as_float(__ldg(&v.vox[(size_t)pool * kBV + (x & 7) + 8 * (y & 7) + 64 * (z & 7)].x));
+    const int ix = lx + (n & 1), iy = ly + ((n >> 1) & 1), iz = lz + ((n >> 2) & 1);
+    const int pn = nb[(ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3)];
+    if (pn < 0) return false;
+    F[n] = __uint_as_float(__ldg(&v.vox[(size_t)pn * kBV + (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7)].x));
     if (F[n] != F[n]) return false;
   }
   return true;

@@ -45,9 +45,9 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
   const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
   const int bx = kx >> 3, by = ky >> 3, bz = kz >> 3;
   uint2 c[8];
+  const int pool = hash_find(v, bx, by, bz);
+  if (pool < 0) return false;
   if (lx < 7 && ly < 7 && lz < 7) {
-    const int pool = hash_find(v, bx, by, bz);
-    if (pool < 0) return false;
     const uint2* base = v.vox + (size_t)pool * kBV + lx + 8 * ly + 64 * lz;
     c[0] = __ldg(base);
     c[1] = __ldg(base + 1);
@@ -58,18 +58,16 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
     c[6] = __ldg(base + 72);
     c[7] = __ldg(base + 73);
   } else {
-    int pools[8];
-#pragma unroll
-    for (int n = 0; n < 8; ++n) pools[n] = -2;
+    // the cell straddles blocks: the neighbours' pools come from the table
+    const int4 n0 = __ldg(v.nbr + 2 * (size_t)pool), n1 = __ldg(v.nbr + 2 * (size_t)pool + 1);
+    const int nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      const int ox = (n & 1) && lx == 7, oy = ((n >> 1) & 1) && ly == 7, oz = ((n >> 2) & 1) && lz == 7;
-      const int slot = ox + 2 * oy + 4 * oz;
-      if (pools[slot] == -2) pools[slot] = hash_find(v, bx + ox, by + oy, bz + oz);
-      const int pool = pools[slot];
-      if (pool < 0) return false;
-      const int ix = (lx + (n & 1)) & 7, iy = (ly + ((n >> 1) & 1)) & 7, iz = (lz + ((n >> 2) & 1)) & 7;
-      c[n] = __ldg(v.vox + (size_t)pool * kBV + ix + 8 * iy + 64 * iz);
+      const int ix = lx + (n & 1), iy = ly + ((n >> 1) & 1), iz = lz + ((n >> 2) & 1);
+      const int slot = (ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3);
+      const int pn = nb[slot];
+      if (pn < 0) return false;
+      c[n] = __ldg(v.vox + (size_t)pn * kBV + (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
     }
   }
   float F[8];
@@ -89,16 +87,17 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
   gV[2] = (c1 - c0) * p.inv_voxel;
   *colour = col;
   if (col) {
-    float In[8];
+    float In[8];  // intensities x 255e4, scaled once below
 #pragma unroll
-    for (int n = 0; n < 8; ++n) In[n] = rgb_intensity(c[n].y);
+    for (int n = 0; n < 8; ++n) In[n] = rgb_intensity_raw(c[n].y);
     const float d00 = lerpf(In[0], In[1], fx), d10 = lerpf(In[2], In[3], fx);
     const float d01 = lerpf(In[4], In[5], fx), d11 = lerpf(In[6], In[7], fx);
     const float d0 = lerpf(d00, d10, fy), d1 = lerpf(d01, d11, fy);
-    *I = lerpf(d0, d1, fz);
-    gI[0] = lerpf(lerpf(In[1] - In[0], In[3] - In[2], fy), lerpf(In[5] - In[4], In[7] - In[6], fy), fz) * p.inv_voxel;
-    gI[1] = lerpf(lerpf(In[2] - In[0], In[3] - In[1], fx), lerpf(In[6] - In[4], In[7] - In[5], fx), fz) * p.inv_voxel;
-    gI[2] = (d1 - d0) * p.inv_voxel;
+    const float gs = kIntensityScale * p.inv_voxel;
+    *I = lerpf(d0, d1, fz) * kIntensityScale;
+    gI[0] = lerpf(lerpf(In[1] - In[0], In[3] - In[2], fy), lerpf(In[5] - In[4], In[7] - In[6], fy), fz) * gs;
+    gI[1] = lerpf(lerpf(In[2] - In[0], In[3] - In[1], fx), lerpf(In[6] - In[4], In[7] - In[5], fx), fz) * gs;
+    gI[2] = (d1 - d0) * gs;
   }
   return true;
 }
@@ -434,7 +433,7 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         if (colour) {
           const uint8_t* cp = f.rgb + 3 * (size_t)idx;
           const unsigned cc = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
-          const float rc = I - rgb_intensity(cc);
+          const float rc = I - rgb_intensity_raw(cc) * kIntensityScale;
           const float Jc[6] = {gI[0], gI[1], gI[2], py * gI[2] - pz * gI[1], pz * gI[0] - px * gI[2],
                                px * gI[1] - py * gI[0]};
           add_jtj(acc, Jc, rc, p.w_c);

@@ -28,6 +28,7 @@ struct rf_volume {
   uint2* d_vox = nullptr;
   uint8_t* d_W = nullptr;
   int4* d_coords = nullptr;
+  int4* d_nbr = nullptr;
   int* d_nblocks = nullptr;
   unsigned* d_status = nullptr;
 
