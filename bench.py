@@ -194,6 +194,51 @@ def cpu_baseline(n_frames: int = 4):
                       f"({1.0 / full:.3f} frames/s)"}
 
 
+def run_batch(R, frames, K, cam, dev, stream, flush, args):
+    """S streams (one volume each, the same rendered sequence) processed in
+    lockstep batches through rf_batch_process: aggregate frames/s and the
+    per-batch latency (every frame of a batch completes at the batch's end)."""
+    import torch
+    S = args.batch_streams
+    vols = [R.Volume(n_buckets=1 << 18, max_blocks=60_000, max_width=cam.width, max_height=cam.height,
+                     voxel_size=VOXEL, trunc=TAU) for _ in range(S)]
+    batch = R.Batch(vols)
+    n = min(len(frames), args.warmup + args.batch_steps)
+    d_depth = [torch.from_numpy(f[0].astype(np.int32)).to(dev).to(torch.uint16).contiguous() for f in frames[:n]]
+    d_rgb = [torch.from_numpy(f[1]).to(dev).contiguous() for f in frames[:n]]
+    T = [torch.as_tensor(frames[0][2], device=dev).contiguous() for _ in range(S)]
+    Tn = [torch.empty(4, 4, dtype=torch.float64, device=dev) for _ in range(S)]
+
+    def step(i):
+        fr = [vols[k].frame(d_depth[i], d_rgb[i], K) for k in range(S)]
+        batch.process(fr, T, Tn, None, stream)
+
+    for i in range(args.warmup):
+        step(i)
+        T, Tn = Tn, T
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(args.warmup, n):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(i)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        T, Tn = Tn, T
+    for v in vols:
+        v.sync()
+    batch.close()
+    for v in vols:
+        v.close()
+    return {"streams": S, "workload": "static room 640x480 per stream (one volume each, voxel 1 cm)",
+            "frames_per_s": S * len(ms) / (sum(ms) / 1000.0), "batches": len(ms),
+            "batch_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                         "mean": statistics.mean(ms)},
+            "note": "lockstep batches via rf_batch_process; a frame's latency is its batch's time"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +247,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--batch-streams", type=int, default=32)
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -333,6 +380,10 @@ def main():
     # dilation (4), integration: prep, tile maxima, frustum, cull, update,
     # neighbour tables (6)
     launches_per_frame = 2 + 4 + 6
+    batch = None
+    if args.batch_streams > 0:
+        batch = run_batch(R, frames, K, cam, dev, stream, flush, args)
+
     if rank == 0:
         st = vol.stats()
         line = {
@@ -361,6 +412,7 @@ def main():
             "work": {"updated_voxels": statistics.mean(upd), "new_blocks": statistics.mean(newb),
                      "candidates": statistics.mean(p.candidates for p in profs), "blocks": st.n_blocks,
                      "guard_pixels": statistics.mean(p.guard_pixels for p in profs)},
+            "batch": batch,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_frame * args.steps,

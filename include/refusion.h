@@ -207,6 +207,29 @@ rf_status rf_process_frame_host(rf_volume* vol, int height, int width, const dou
                                 const uint16_t* depth_host, const uint8_t* rgb_host, const double T_init_host[16],
                                 double T_out_host[16], uint8_t* mask_host, void* stream);
 
+/* Batches: one frame for each of n volumes (independent camera streams, any
+ * mix of resolutions and voxel sizes) per call.  The two registrations of all
+ * streams run as one cooperative launch each, with one group of CTAs per
+ * stream sized by its pixel count (the groups never wait on each other); the
+ * masks and integrations of the streams run concurrently.  A stream's result
+ * is bit-identical to processing it alone with rf_process_frame (partial
+ * sums are taken over fixed pixel chunks, not per CTA).
+ * rf_batch_create: n <= number of SMs; volumes on the current device, each
+ * at most once.  It allocates the batch's streams and events; each new batch
+ * shape (frame sizes, intrinsics, which streams are on their first frame)
+ * captures a graph and allocates its small descriptor buffers on first use.
+ * rf_batch_process: frames, T_init_dev, T_out_dev, mask_dev (nullable, and
+ * entries nullable) are arrays of n, device pointers as in rf_process_frame.
+ * Asynchronous on `stream`; kernel-detected errors go to each volume's
+ * rf_sync_status.  A batch must not run concurrently with other work on its
+ * volumes. */
+typedef struct rf_batch rf_batch;
+rf_status rf_batch_create(rf_volume* const* vols, int n, rf_batch** out);
+rf_status rf_batch_destroy(rf_batch* batch);
+rf_status rf_batch_process(rf_batch* batch, const rf_frame* frames, const double* const* T_init_dev,
+                           double* const* T_out_dev, uint8_t* const* mask_dev, void* stream);
+const char* rf_batch_last_error(rf_batch* batch);
+
 /* Zero-crossing surface of the TSDF (the mesh of Sec. I) by marching
  * tetrahedra over cells whose 8 corners are observed; triangle soup, normals
  * towards positive SDF.  verts_dev: float [cap_tris][3][3]; colors_dev: uint8

@@ -280,6 +280,177 @@ rf_status run_frame(rf_volume* vol, const rf_frame* fr, bool first, cudaGraphExe
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// batches: one frame for each of several volumes (independent camera streams)
+// ---------------------------------------------------------------------------
+struct rf_batch_graph {
+  std::vector<double> sig;  // per stream: H, W, fx, fy, cx, cy, first
+  cudaGraphExec_t exec = nullptr;
+  RegDesc* d_desc = nullptr;  // [2][n]: first and second registration
+  int* d_cta = nullptr;       // CTA -> stream, then the n + 1 group starts
+};
+
+struct rf_batch {
+  std::vector<rf_volume*> vols;
+  int device = 0;
+  static constexpr int kAux = 8;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kAux] = {};
+  std::vector<rf_batch_graph> graphs;
+  std::string last_error;
+};
+
+namespace {
+
+rf_status batch_error(rf_batch* b, rf_status s, const std::string& msg) {
+  b->last_error = msg;
+  return s;
+}
+
+// Fork: every auxiliary stream waits for the work enqueued on cs so far.
+void fork_aux(rf_batch* b, cudaStream_t cs) {
+  cudaEventRecord(b->fork_ev, cs);
+  for (int k = 0; k < rf_batch::kAux; ++k) cudaStreamWaitEvent(b->aux[k], b->fork_ev, 0);
+}
+
+// Join: cs waits for every auxiliary stream.
+void join_aux(rf_batch* b, cudaStream_t cs) {
+  for (int k = 0; k < rf_batch::kAux; ++k) {
+    cudaEventRecord(b->join_ev[k], b->aux[k]);
+    cudaStreamWaitEvent(cs, b->join_ev[k], 0);
+  }
+}
+
+// CTA groups of the batched registration: at least one CTA per stream, the
+// rest in proportion to the stream's pixel count (largest remainders).
+std::vector<int> split_ctas(const std::vector<double>& weight, int total) {
+  const int n = (int)weight.size();
+  std::vector<int> cnt(n, 1);
+  double wsum = 0.0;
+  for (double w : weight) wsum += w;
+  const int spare = total - n;
+  std::vector<std::pair<double, int>> rem;
+  int given = 0;
+  for (int i = 0; i < n; ++i) {
+    const double share = spare * weight[i] / wsum;
+    const int whole = (int)share;
+    cnt[i] += whole;
+    given += whole;
+    rem.push_back({share - whole, i});
+  }
+  std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first != y.first ? x.first > y.first : x.second < y.second;
+  });
+  for (int k = 0; k < spare - given && k < n; ++k) cnt[rem[k].second]++;
+  return cnt;
+}
+
+rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<double>& sig, rf_batch_graph* out) {
+  const int n = (int)b->vols.size();
+  std::vector<DevFrame> f(n);
+  std::vector<int> nf;  // streams past their first frame (tracked)
+  for (int i = 0; i < n; ++i) {
+    rf_frame staged = frames[i];
+    staged.depth = b->vols[i]->d_depth;
+    staged.rgb = b->vols[i]->d_rgb;
+    f[i] = make_dev_frame(&staged);
+    if (b->vols[i]->frames > 0) nf.push_back(i);
+  }
+  const int total_ctas = b->vols[0]->reg_grid;
+  std::vector<RegDesc> desc(2 * (nf.empty() ? 1 : nf.size()));
+  std::vector<int> cta;
+  if (!nf.empty()) {
+    std::vector<double> w;
+    for (int i : nf) {
+      rf_volume* v = b->vols[i];
+      desc[w.size()] = make_reg_desc(v, f[i], v->d_T, nullptr, v->d_T + 16, nullptr);
+      desc[nf.size() + w.size()] = make_reg_desc(v, f[i], v->d_T + 16, v->d_mask, v->d_T + 32, v->d_info);
+      w.push_back((double)frames[i].width * frames[i].height);
+    }
+    const std::vector<int> cnt = split_ctas(w, total_ctas);
+    std::vector<int> first(nf.size() + 1, 0);
+    for (size_t k = 0; k < nf.size(); ++k) {
+      first[k + 1] = first[k] + cnt[k];
+      for (int c = 0; c < cnt[k]; ++c) cta.push_back((int)k);
+    }
+    cta.insert(cta.end(), first.begin(), first.end());
+  }
+  cudaError_t e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
+  if (e == cudaSuccess) e = cudaMalloc(&out->d_cta, sizeof(int) * (cta.size() + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !cta.empty())
+    e = cudaMemcpy(out->d_cta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch descriptors: ") + cudaGetErrorString(e));
+  std::vector<bool> prof(n);
+  for (int i = 0; i < n; ++i) {
+    prof[i] = b->vols[i]->profiling;
+    b->vols[i]->profiling = false;  // per-volume profiling events are not used in batches
+  }
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  rf_status s = RF_OK;
+  if (e != cudaSuccess) {
+    s = batch_error(b, RF_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  } else {
+    const int nt = (int)nf.size();
+    const RegDesc* d1 = out->d_desc;
+    const RegDesc* d2 = out->d_desc + nt;
+    const int* cta_stream = out->d_cta;
+    const int* group_first = out->d_cta + total_ctas;
+    if (nt > 0) {
+      for (int i : nf) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
+      s = launch_register_batch(b->vols[nf[0]], d1, cta_stream, group_first, total_ctas, cs);
+      // residual seeds and erosion: concurrent; flood fills (cooperative): one at a time
+      fork_aux(b, cs);
+      for (int k = 0; k < nt && !s; ++k) {
+        rf_volume* v = b->vols[nf[k]];
+        s = launch_mask_pre(v, f[nf[k]], v->d_T + 16, b->aux[k % rf_batch::kAux]);
+      }
+      join_aux(b, cs);
+      for (int k = 0; k < nt && !s; ++k) s = launch_mask_ff(b->vols[nf[k]], f[nf[k]], cs);
+      fork_aux(b, cs);
+      for (int k = 0; k < nt && !s; ++k) {
+        rf_volume* v = b->vols[nf[k]];
+        s = launch_mask_post(v, f[nf[k]], v->d_mask, b->aux[k % rf_batch::kAux]);
+      }
+      join_aux(b, cs);
+      for (int i : nf) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
+      if (!s) s = launch_register_batch(b->vols[nf[0]], d2, cta_stream, group_first, total_ctas, cs);
+    }
+    // integrations: concurrent
+    fork_aux(b, cs);
+    for (int i = 0; i < n && !s; ++i) {
+      rf_volume* v = b->vols[i];
+      cudaStream_t a = b->aux[i % rf_batch::kAux];
+      if (v->frames == 0) {
+        cudaMemsetAsync(v->d_mask, 0, (size_t)f[i].H * f[i].W, a);
+        s = launch_integrate(v, f[i], v->d_T, nullptr, a);
+        cudaMemcpyAsync(v->d_T + 32, v->d_T, 16 * sizeof(double), cudaMemcpyDeviceToDevice, a);
+      } else {
+        s = launch_integrate(v, f[i], v->d_T + 32, v->d_mask, a);
+      }
+    }
+    join_aux(b, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (!s && ce != cudaSuccess) s = batch_error(b, RF_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(ce));
+    if (!s) {
+      ce = cudaGraphInstantiate(&out->exec, graph, 0);
+      if (ce != cudaSuccess) s = batch_error(b, RF_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(ce));
+    } else if (s != RF_OK && b->last_error.empty()) {
+      b->last_error = b->vols[0]->last_error;
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  if (cs) cudaStreamDestroy(cs);
+  for (int i = 0; i < n; ++i) b->vols[i]->profiling = prof[i];
+  out->sig = sig;
+  return s;
+}
+
+}  // namespace
+
 extern "C" {
 
 rf_status rf_default_params(rf_params* p) {
@@ -370,6 +541,7 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
     return s;
   }
   const size_t npix = (size_t)max_width * max_height;
+  vol->max_chunks = (int)((npix + 511) / 512);
   vol->reg_grid = register_max_grid(vol->device);
   if (vol->reg_grid > vol->sm_count) vol->reg_grid = vol->sm_count;
   if (vol->reg_grid < 1) {
@@ -384,7 +556,7 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
       (s = dalloc(vol, &vol->d_coords, (size_t)max_blocks, "coords")) ||
       (s = dalloc(vol, &vol->d_nbr, 2 * (size_t)max_blocks, "neighbour tables")) || (s = dalloc(vol, &vol->d_nblocks, 1, "pool")) ||
       (s = dalloc(vol, &vol->d_status, 1, "status")) || (s = dalloc(vol, &vol->d_regbar, 2, "barrier")) ||
-      (s = dalloc(vol, &vol->d_partials, (size_t)2 * 29 * vol->reg_grid + 2, "partials")) ||
+      (s = dalloc(vol, &vol->d_partials, (size_t)2 * 29 * vol->max_chunks + 2, "partials")) ||
       (s = dalloc(vol, &vol->d_seeds, npix, "seeds")) || (s = dalloc(vol, &vol->d_md, npix, "mask work")) ||
       (s = dalloc(vol, &vol->d_ff, (size_t)p->max_ff_sweeps + 2, "flood-fill words")) ||
       (s = dalloc(vol, &vol->d_integ, 1, "integ")) || (s = dalloc(vol, &vol->d_tilemax, ntiles, "tiles")) ||
@@ -684,6 +856,106 @@ rf_status rf_get_profile(rf_volume* vol, void* stream, rf_profile* out) {
   out->updated_voxels = (int64_t)is.updated;
   out->new_blocks = is.new_blocks;
   out->guard_pixels = guard;
+  return RF_OK;
+}
+
+rf_status rf_batch_create(rf_volume* const* vols, int n, rf_batch** out) {
+  if (!out) return RF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!vols || n < 1) return set_error(nullptr, RF_ERR_INVALID_ARG, "rf_batch_create: need at least one volume");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return set_error(nullptr, RF_ERR_CUDA, "no CUDA device");
+  for (int i = 0; i < n; ++i) {
+    if (!vols[i]) return set_error(nullptr, RF_ERR_INVALID_ARG, "rf_batch_create: NULL volume");
+    if (vols[i]->device != dev) return set_error(nullptr, RF_ERR_INVALID_ARG, "volumes on different devices");
+    for (int j = 0; j < i; ++j)
+      if (vols[j] == vols[i]) return set_error(nullptr, RF_ERR_INVALID_ARG, "a volume appears twice in a batch");
+  }
+  if (n > vols[0]->reg_grid)
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "rf_batch_create: at most %d streams per batch on this device",
+                     vols[0]->reg_grid);
+  rf_batch* b = new rf_batch();
+  b->vols.assign(vols, vols + n);
+  b->device = dev;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  for (int k = 0; k < rf_batch::kAux && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    rf_batch_destroy(b);
+    return set_error(nullptr, RF_ERR_CUDA, "rf_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return RF_OK;
+}
+
+rf_status rf_batch_destroy(rf_batch* b) {
+  if (!b) return RF_OK;
+  cudaDeviceSynchronize();
+  for (auto& g : b->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.d_desc) cudaFree(g.d_desc);
+    if (g.d_cta) cudaFree(g.d_cta);
+  }
+  for (int k = 0; k < rf_batch::kAux; ++k) {
+    if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+    if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  delete b;
+  return RF_OK;
+}
+
+const char* rf_batch_last_error(rf_batch* b) { return b ? b->last_error.c_str() : ""; }
+
+rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* const* T_init_dev,
+                           double* const* T_out_dev, uint8_t* const* mask_dev, void* stream) {
+  if (!b || !frames || !T_init_dev || !T_out_dev) return RF_ERR_INVALID_ARG;
+  const int n = (int)b->vols.size();
+  std::vector<double> sig;
+  for (int i = 0; i < n; ++i) {
+    if (!frame_ok(b->vols[i], &frames[i])) return batch_error(b, RF_ERR_INVALID_ARG, "invalid frame in batch");
+    if (!T_init_dev[i] || !T_out_dev[i]) return batch_error(b, RF_ERR_INVALID_ARG, "NULL pose in batch");
+    const rf_frame& fr = frames[i];
+    sig.insert(sig.end(), {(double)fr.height, (double)fr.width, fr.fx, fr.fy, fr.cx, fr.cy,
+                           b->vols[i]->frames == 0 ? 1.0 : 0.0});
+  }
+  rf_batch_graph* g = nullptr;
+  for (auto& x : b->graphs)
+    if (x.sig == sig) g = &x;
+  if (!g) {
+    b->graphs.emplace_back();
+    g = &b->graphs.back();
+    rf_status s = batch_capture(b, frames, sig, g);
+    if (s != RF_OK) {
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      if (g->d_desc) cudaFree(g->d_desc);
+      if (g->d_cta) cudaFree(g->d_cta);
+      b->graphs.pop_back();
+      return s;
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) {
+    rf_volume* v = b->vols[i];
+    const size_t npix = (size_t)frames[i].height * frames[i].width;
+    cudaMemcpyAsync(v->d_depth, frames[i].depth, npix * 2, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(v->d_rgb, frames[i].rgb, npix * 3, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(v->d_T, T_init_dev[i], 16 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  }
+  cudaError_t e = cudaGraphLaunch(g->exec, st);
+  if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+  for (int i = 0; i < n; ++i) {
+    rf_volume* v = b->vols[i];
+    cudaMemcpyAsync(T_out_dev[i], v->d_T + 32, 16 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (mask_dev && mask_dev[i])
+      cudaMemcpyAsync(mask_dev[i], v->d_mask, (size_t)frames[i].height * frames[i].width, cudaMemcpyDeviceToDevice,
+                      st);
+    v->frames++;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch copies: ") + cudaGetErrorString(e));
   return RF_OK;
 }
 

@@ -81,6 +81,28 @@ struct DevFrame {
   const uint8_t* rgb;
 };
 
+struct LMConst {
+  double lambda0, eps_t, eps_r;
+  long long min_valid;
+  int iters[3], strides[3];
+};
+
+// Everything one registration needs (one camera stream).
+struct RegDesc {
+  DevVol v;
+  DevFrame f;
+  DevParams p;
+  const uint8_t* mask;
+  const double* T_init;
+  double* T_out;
+  rf_track_info* info;
+  LMConst c;
+  float* partials;
+  int max_chunks;
+  unsigned* bar;
+  unsigned* status;
+};
+
 // Quantised pose and the frustum search region of one integration.
 struct IntegState {
   long long A[9];  // llround(R^T * 2^30), world -> camera
@@ -145,11 +167,16 @@ __device__ __forceinline__ int hash_find(const DevVol& v, int bx, int by, int bz
 // 255e4 (exact integer arithmetic, one conversion).
 constexpr float kIntensityScale = 1.0f / 2550000.0f;
 __device__ __forceinline__ float rgb_intensity_raw(unsigned c) {
-  const int s = 2126 * (int)(c & 255u) + 7152 * (int)((c >> 8) & 255u) + 722 * (int)((c >> 16) & 255u);
+  // two 16x8-bit dot products: (2126, 7152) . (R, G) + (722, 0) . (B, byte 3)
+  const unsigned s = __dp2a_hi(722u, c, __dp2a_lo(2126u | (7152u << 16), c, 0u));
   return (float)s;
 }
 
 __device__ __forceinline__ bool pixel_valid(const DevParams& p, unsigned raw) {
+  if (p.du_um < 32768) {  // raw * du fits 31 bits
+    const int D = (int)raw * (int)p.du_um;
+    return raw != 0 && D >= (int)p.dmin_um && D <= (int)p.dmax_um;
+  }
   const long long D = (long long)raw * p.du_um;
   return raw != 0 && D >= p.dmin_um && D <= p.dmax_um;
 }
@@ -239,6 +266,14 @@ enum ProfEvent { EV_FRAME0, EV_TRACK1_END, EV_MASK_END, EV_TRACK2_END, EV_INTEG0
                  EV_COUNT };
 void prof_record(rf_volume* vol, int ev, cudaStream_t st);
 rf_status run_mesh(rf_volume* vol, float* verts, uint8_t* colors, int64_t cap, int64_t* n, cudaStream_t st);
+RegDesc make_reg_desc(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
+                      rf_track_info* info);
+rf_status launch_register_batch(rf_volume* vol, const RegDesc* descs, const int* cta_stream, const int* first,
+                                int total_ctas, cudaStream_t st);
+// the three parts of launch_mask (the flood fill is the cooperative one)
+rf_status launch_mask_pre(rf_volume* vol, const DevFrame& f, const double* T, cudaStream_t st);
+rf_status launch_mask_ff(rf_volume* vol, const DevFrame& f, cudaStream_t st);
+rf_status launch_mask_post(rf_volume* vol, const DevFrame& f, uint8_t* mask_out, cudaStream_t st);
 // neighbour tables of the blocks allocated since *lo_ptr (or since lo when lo_ptr is null)
 rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st);
 }  // namespace rf

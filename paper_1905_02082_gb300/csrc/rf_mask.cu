@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uin
 
 }  // namespace
 
-rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_t* mask_out, cudaStream_t st) {
+rf_status launch_mask_pre(rf_volume* vol, const DevFrame& f, const double* T, cudaStream_t st) {
   const int n = f.H * f.W;
   const int blocks = (n + 255) / 256;
   rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_guard, 0, sizeof(unsigned), st), "guard reset");
@@ -267,6 +267,10 @@ rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_
   s = check_cuda(vol, cudaMemsetAsync(vol->d_ff, 0, sizeof(unsigned) * (2 + vol->p.max_ff_sweeps), st),
                  "flood-fill reset");
   if (s != RF_OK) return s;
+  return check_cuda(vol, cudaGetLastError(), "mask launch");
+}
+
+rf_status launch_mask_ff(rf_volume* vol, const DevFrame& f, cudaStream_t st) {
   const int ntiles = ((f.W + kFFW - 1) / kFFW) * ((f.H + kFFH - 1) / kFFH);
   const int grid = ntiles < vol->ff_grid ? ntiles : vol->ff_grid;
   cudaLaunchConfig_t cfg = {};
@@ -278,13 +282,23 @@ rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  s = check_cuda(vol,
-                 cudaLaunchKernelEx(&cfg, k_floodfill, vol->d_md, f.depth, f.H, f.W, vol->dp.theta_ppm, vol->d_ff,
-                                    vol->p.max_ff_sweeps, vol->d_status),
-                 "flood-fill launch");
-  if (s != RF_OK) return s;
-  k_dilate<<<blocks, 256, 0, st>>>(vol->d_md, f.H, f.W, mask_out);
+  return check_cuda(vol,
+                    cudaLaunchKernelEx(&cfg, k_floodfill, vol->d_md, f.depth, f.H, f.W, vol->dp.theta_ppm, vol->d_ff,
+                                       vol->p.max_ff_sweeps, vol->d_status),
+                    "flood-fill launch");
+}
+
+rf_status launch_mask_post(rf_volume* vol, const DevFrame& f, uint8_t* mask_out, cudaStream_t st) {
+  const int n = f.H * f.W;
+  k_dilate<<<(n + 255) / 256, 256, 0, st>>>(vol->d_md, f.H, f.W, mask_out);
   return check_cuda(vol, cudaGetLastError(), "mask launch");
+}
+
+rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_t* mask_out, cudaStream_t st) {
+  rf_status s = launch_mask_pre(vol, f, T, st);
+  if (s == RF_OK) s = launch_mask_ff(vol, f, st);
+  if (s == RF_OK) s = launch_mask_post(vol, f, mask_out, st);
+  return s;
 }
 
 int floodfill_max_grid(int device) {

@@ -71,20 +71,22 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
     }
   }
   float F[8];
-  bool col = true;
 #pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    F[n] = __uint_as_float(c[n].x);
-    if (F[n] != F[n]) return false;  // never observed
-    col &= (c[n].y >> 24) != 0u;
-  }
+  for (int n = 0; n < 8; ++n) F[n] = __uint_as_float(c[n].x);
   const float c00 = lerpf(F[0], F[1], fx), c10 = lerpf(F[2], F[3], fx);
   const float c01 = lerpf(F[4], F[5], fx), c11 = lerpf(F[6], F[7], fx);
   const float c0 = lerpf(c00, c10, fy), c1 = lerpf(c01, c11, fy);
   *V = lerpf(c0, c1, fz);
+  // a never-observed corner stores NaN; every corner enters V with its
+  // weight (0 * NaN = NaN), so one test covers all eight
+  if (*V != *V) return false;
   gV[0] = lerpf(lerpf(F[1] - F[0], F[3] - F[2], fy), lerpf(F[5] - F[4], F[7] - F[6], fy), fz) * p.inv_voxel;
   gV[1] = lerpf(lerpf(F[2] - F[0], F[3] - F[1], fx), lerpf(F[6] - F[4], F[7] - F[5], fx), fz) * p.inv_voxel;
   gV[2] = (c1 - c0) * p.inv_voxel;
+  // colour weights in the top bytes: their minimum over the corners
+  unsigned wmin = __vminu4(__vminu4(__vminu4(c[0].y, c[1].y), __vminu4(c[2].y, c[3].y)),
+                           __vminu4(__vminu4(c[4].y, c[5].y), __vminu4(c[6].y, c[7].y)));
+  const bool col = (wmin >> 24) != 0u;
   *colour = col;
   if (col) {
     float In[8];  // intensities x 255e4, scaled once below
@@ -115,11 +117,6 @@ __device__ __forceinline__ void add_jtj(float* acc, const float J[6], float r, f
   acc[27] += w * r * r;
 }
 
-struct LMConst {
-  double lambda0, eps_t, eps_r;
-  long long min_valid;
-  int iters[3], strides[3];
-};
 
 // FP64 reciprocal: FP32 seed refined by two FP64 Newton steps (relative
 // error ~(2^-23)^4, i.e. full double precision), far cheaper than a double
@@ -365,19 +362,23 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
 constexpr int kRegThreads = 512;
 constexpr int kRegWarps = kRegThreads / 32;
 
-// One whole registration (see the file comment).  partials: 2 x 29 x gridDim
-// floats (double-buffered by evaluation parity); bar: 2 zeroed words.
-__global__ void __launch_bounds__(kRegThreads, 1)
-    k_register(DevVol v, DevFrame f, DevParams p, const uint8_t* __restrict__ mask, const double* __restrict__ T_init,
-               double* __restrict__ T_out, rf_track_info* info_out, LMConst c, float* partials, unsigned* bar,
-               unsigned* status) {
+// Pixels per partial sum: a fixed chunk of the sampled pixels of a level
+// (512, or 2048 from 2^18 pixels), so the partials, and thus the result, do
+// not depend on how many CTAs run the registration.
+__device__ __forceinline__ int chunk_pixels(int npix) { return npix >= (1 << 18) ? 4 * kRegThreads : kRegThreads; }
+
+// One whole registration (see the file comment) run by a group of G CTAs,
+// this CTA being number lb of the group.  d.partials: 2 x 29 x max chunks
+// floats (double-buffered by evaluation parity); d.bar: a zeroed counter.
+__device__ void register_body(const RegDesc& d, int lb, int G) {
   __shared__ LMShared S;
   __shared__ float red[kRegWarps][29];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int G = gridDim.x;
+  const DevFrame& f = d.f;
+  const DevParams& p = d.p;
   if (threadIdx.x < 16) {
-    S.T[threadIdx.x] = T_init[threadIdx.x];
-    S.Tc[threadIdx.x] = T_init[threadIdx.x];
+    S.T[threadIdx.x] = d.T_init[threadIdx.x];
+    S.Tc[threadIdx.x] = d.T_init[threadIdx.x];
   }
   if (threadIdx.x == 0) {
     S.done = 0;
@@ -399,72 +400,84 @@ __global__ void __launch_bounds__(kRegThreads, 1)
   __syncthreads();
   int eval = 0;
   for (int l = 0; l < 3; ++l) {
-    const int stride = c.strides[l];
+    const int stride = d.c.strides[l];
     const int Ws = (f.W + stride - 1) / stride, Hs = (f.H + stride - 1) / stride;
     const int npix = Ws * Hs;
-    const int iters = c.iters[l];
+    const int chunk = chunk_pixels(npix);
+    const int nchunks = (npix + chunk - 1) / chunk;
+    // row = i / Ws by a reciprocal multiply (off by at most one for i < 2^32),
+    // then one integer correction step
+    const unsigned long long magic = (0x100000000ull + Ws - 1) / Ws;
+    const int iters = d.c.iters[l];
     for (int it = 0; it <= iters; ++it) {
       const int mode = it == 0 ? 0 : 1;
-      if (mode == 1 && S.done) break;  // identical decision in every CTA
+      if (mode == 1 && S.done) break;  // identical decision in every CTA of the group
       const float* Tf = mode == 0 ? S.Rf : S.Rcf;
       const float R0 = Tf[0], R1 = Tf[1], R2 = Tf[2], R3 = Tf[3], R4 = Tf[4], R5 = Tf[5], R6 = Tf[6], R7 = Tf[7],
                   R8 = Tf[8], t0 = Tf[9], t1 = Tf[10], t2 = Tf[11];
-      float acc[29];
+      float* part = d.partials + (size_t)(eval & 1) * 29 * d.max_chunks;
+      for (int ch = lb; ch < nchunks; ch += G) {
+        float acc[29];
 #pragma unroll
-      for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
-      for (int i = blockIdx.x * kRegThreads + threadIdx.x; i < npix; i += G * kRegThreads) {
-        const int u = (i % Ws) * stride, vv = (i / Ws) * stride;
-        const int idx = vv * f.W + u;
-        const unsigned raw = __ldg(f.depth + idx);
-        if (!pixel_valid(p, raw)) continue;
-        if (mask && __ldg(mask + idx)) continue;
-        const float D = (float)raw * p.inv_depth_scale;
-        const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
-        const float px = R0 * x + R1 * y + R2 * D + t0;
-        const float py = R3 * x + R4 * y + R5 * D + t1;
-        const float pz = R6 * x + R7 * y + R8 * D + t2;
-        float V, gV[3], I, gI[3];
-        bool colour;
-        if (!model_sample(v, p, px, py, pz, &V, gV, &I, gI, &colour)) continue;
-        const float Jd[6] = {gV[0], gV[1], gV[2], py * gV[2] - pz * gV[1], pz * gV[0] - px * gV[2],
-                             px * gV[1] - py * gV[0]};
-        add_jtj(acc, Jd, V, 1.0f);
-        acc[28] += 1.0f;
-        if (colour) {
-          const uint8_t* cp = f.rgb + 3 * (size_t)idx;
-          const unsigned cc = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
-          const float rc = I - rgb_intensity_raw(cc) * kIntensityScale;
-          const float Jc[6] = {gI[0], gI[1], gI[2], py * gI[2] - pz * gI[1], pz * gI[0] - px * gI[2],
-                               px * gI[1] - py * gI[0]};
-          add_jtj(acc, Jc, rc, p.w_c);
+        for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
+        const int end = min(npix, (ch + 1) * chunk);
+        for (int i = ch * chunk + threadIdx.x; i < end; i += kRegThreads) {
+          int row = (int)(((unsigned long long)i * magic) >> 32);
+          if (row * Ws > i) --row;
+          else if ((row + 1) * Ws <= i) ++row;
+          const int u = (i - row * Ws) * stride, vv = row * stride;
+          const int idx = vv * f.W + u;
+          const unsigned raw = __ldg(f.depth + idx);
+          if (!pixel_valid(p, raw)) continue;
+          if (d.mask && __ldg(d.mask + idx)) continue;
+          const float D = (float)raw * p.inv_depth_scale;
+          const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
+          const float px = R0 * x + R1 * y + R2 * D + t0;
+          const float py = R3 * x + R4 * y + R5 * D + t1;
+          const float pz = R6 * x + R7 * y + R8 * D + t2;
+          float V, gV[3], I, gI[3];
+          bool colour;
+          if (!model_sample(d.v, p, px, py, pz, &V, gV, &I, gI, &colour)) continue;
+          const float Jd[6] = {gV[0], gV[1], gV[2], py * gV[2] - pz * gV[1], pz * gV[0] - px * gV[2],
+                               px * gV[1] - py * gV[0]};
+          add_jtj(acc, Jd, V, 1.0f);
+          acc[28] += 1.0f;
+          if (colour) {
+            const uint8_t* cp = f.rgb + 3 * (size_t)idx;
+            const unsigned cc =
+                (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
+            const float rc = I - rgb_intensity_raw(cc) * kIntensityScale;
+            const float Jc[6] = {gI[0], gI[1], gI[2], py * gI[2] - pz * gI[1], pz * gI[0] - px * gI[2],
+                                 px * gI[1] - py * gI[0]};
+            add_jtj(acc, Jc, rc, p.w_c);
+          }
         }
-      }
-      // CTA partial: warp shuffles, then the warps in fixed order
+        // chunk partial: warp shuffles, then the warps in fixed order
 #pragma unroll
-      for (int i = 0; i < 29; ++i) {
-        float sv = acc[i];
+        for (int i = 0; i < 29; ++i) {
+          float sv = acc[i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-        if (lane == 0) red[warp][i] = sv;
-      }
-      __syncthreads();
-      float* part = partials + (size_t)(eval & 1) * 29 * G;
-      if (threadIdx.x < 29) {
-        float sv = 0.0f;
+          for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+          if (lane == 0) red[warp][i] = sv;
+        }
+        __syncthreads();
+        if (threadIdx.x < 29) {
+          float sv = 0.0f;
 #pragma unroll
-        for (int w = 0; w < kRegWarps; ++w) sv += red[w][threadIdx.x];
-        part[threadIdx.x * G + blockIdx.x] = sv;
+          for (int w = 0; w < kRegWarps; ++w) sv += red[w][threadIdx.x];
+          part[threadIdx.x * nchunks + ch] = sv;
+        }
+        __syncthreads();
       }
-      if (!grid_sync_counter(bar, (unsigned)(eval + 1) * (unsigned)G, status)) return;
-      // every CTA: FP64 reduction of all partials (L1 bypassed: written by others)
-      // FP32 reduction in a fixed order: lane-strided sums, then a shuffle tree
+      if (!grid_sync_counter(d.bar, (unsigned)(eval + 1) * (unsigned)G, d.status)) return;
+      // every CTA of the group: FP32 reduction of the chunk partials in a fixed
+      // order (lane-strided sums, then a shuffle tree); L1 bypassed
       {
-        // warp w reduces components w and w + 16 (both rows' loads in flight)
-        const int ca = warp, cb = warp + kRegWarps;
-        const float* ra = part + ca * G;
-        const float* rb = part + (cb < 29 ? cb : ca) * G;
+        const int ca = warp, cb = warp + kRegWarps;  // warp w: components w and w + 16
+        const float* ra = part + ca * nchunks;
+        const float* rb = part + (cb < 29 ? cb : ca) * nchunks;
         float fa = 0.0f, fb = 0.0f;
-        for (int k = lane; k < G; k += 32) {
+        for (int k = lane; k < nchunks; k += 32) {
           fa += __ldcg(ra + k);
           fb += __ldcg(rb + k);
         }
@@ -479,20 +492,36 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         }
       }
       __syncthreads();
-      if (warp == 0) lm_step_warp(S, mode, l, it == iters, c, lane);
+      if (warp == 0) lm_step_warp(S, mode, l, it == iters, d.c, lane);
       __syncthreads();
       ++eval;
     }
   }
-  if (blockIdx.x == 0) {
-    if (threadIdx.x < 16) T_out[threadIdx.x] = S.T[threadIdx.x];
-    if (threadIdx.x == 0 && info_out) {
+  if (lb == 0) {
+    if (threadIdx.x < 16) d.T_out[threadIdx.x] = S.T[threadIdx.x];
+    if (threadIdx.x == 0 && d.info) {
       rf_track_info out = S.info;
       out.final_cost = S.fin_N > 0 ? S.fin_E / (double)S.fin_N : 0.0;
       out.final_valid = S.fin_N;
-      *info_out = out;
+      *d.info = out;
     }
   }
+}
+
+// One registration on the whole grid.
+__global__ void __launch_bounds__(kRegThreads, 1) k_register(RegDesc d) { register_body(d, blockIdx.x, gridDim.x); }
+
+// Several independent registrations in one cooperative launch: CTA b runs
+// stream cta_stream[b] as member b - first[s] of a group of first[s+1] -
+// first[s] CTAs.  Groups never wait on each other.
+__global__ void __launch_bounds__(kRegThreads, 1)
+    k_register_batch(const RegDesc* __restrict__ descs, const int* __restrict__ cta_stream,
+                     const int* __restrict__ first) {
+  __shared__ RegDesc sd;
+  const int s = cta_stream[blockIdx.x];
+  if (threadIdx.x == 0) sd = descs[s];
+  __syncthreads();
+  register_body(sd, blockIdx.x - first[s], first[s + 1] - first[s]);
 }
 
 }  // namespace
@@ -504,21 +533,34 @@ int register_max_grid(int device) {
   return per_sm * sms;
 }
 
-rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
-                       rf_track_info* info, cudaStream_t st) {
-  LMConst c;
-  c.lambda0 = vol->p.lm_lambda0;
-  c.eps_t = vol->p.lm_eps_trans;
-  c.eps_r = vol->p.lm_eps_rot;
-  c.min_valid = vol->p.lm_min_valid;
+RegDesc make_reg_desc(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
+                      rf_track_info* info) {
+  RegDesc d;
+  d.v = vol->dv;
+  d.f = f;
+  d.p = vol->dp;
+  d.mask = mask;
+  d.T_init = T_init;
+  d.T_out = T_out;
+  d.info = info;
+  d.c.lambda0 = vol->p.lm_lambda0;
+  d.c.eps_t = vol->p.lm_eps_trans;
+  d.c.eps_r = vol->p.lm_eps_rot;
+  d.c.min_valid = vol->p.lm_min_valid;
   for (int l = 0; l < 3; ++l) {
-    c.iters[l] = vol->p.lm_iters[l];
-    c.strides[l] = vol->p.lm_strides[l];
+    d.c.iters[l] = vol->p.lm_iters[l];
+    d.c.strides[l] = vol->p.lm_strides[l];
   }
-  rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_regbar, 0, 2 * sizeof(unsigned), st), "barrier reset");
-  if (s != RF_OK) return s;
+  d.partials = vol->d_partials;
+  d.max_chunks = vol->max_chunks;
+  d.bar = vol->d_regbar;
+  d.status = vol->d_status;
+  return d;
+}
+
+static rf_status launch_coop(rf_volume* vol, const void* fn, int grid, void** args, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(vol->reg_grid);
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kRegThreads);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -526,10 +568,22 @@ rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return check_cuda(vol,
-                    cudaLaunchKernelEx(&cfg, k_register, vol->dv, f, vol->dp, mask, T_init, T_out, info, c,
-                                       vol->d_partials, vol->d_regbar, vol->d_status),
-                    "registration launch");
+  return check_cuda(vol, cudaLaunchKernelExC(&cfg, fn, args), "registration launch");
+}
+
+rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
+                       rf_track_info* info, cudaStream_t st) {
+  RegDesc d = make_reg_desc(vol, f, T_init, mask, T_out, info);
+  rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_regbar, 0, 2 * sizeof(unsigned), st), "barrier reset");
+  if (s != RF_OK) return s;
+  void* args[] = {&d};
+  return launch_coop(vol, (const void*)k_register, vol->reg_grid, args, st);
+}
+
+rf_status launch_register_batch(rf_volume* vol, const RegDesc* descs, const int* cta_stream, const int* first,
+                                int total_ctas, cudaStream_t st) {
+  void* args[] = {(void*)&descs, (void*)&cta_stream, (void*)&first};
+  return launch_coop(vol, (const void*)k_register_batch, total_ctas, args, st);
 }
 
 }  // namespace rf

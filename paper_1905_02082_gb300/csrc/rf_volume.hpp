@@ -33,7 +33,8 @@ struct rf_volume {
   unsigned* d_status = nullptr;
 
   // registration scratch
-  float* d_partials = nullptr;  // 2 x 29 x reg_grid floats (also the mesh counter)
+  float* d_partials = nullptr;  // 2 x 29 x max_chunks floats (also the mesh counter)
+  int max_chunks = 0;
   unsigned* d_regbar = nullptr;  // grid-barrier words of the registration kernel
   int reg_grid = 0;
 

@@ -76,6 +76,10 @@ SIGNATURES = [
     ("rf_volume_export", _int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, C.POINTER(_i64)]),
     ("rf_volume_import", _int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     ("rf_volume_stats", _int, [_vp, C.POINTER(rf_stats)]),
+    ("rf_batch_create", _int, [_vp, _int, C.POINTER(_vp)]),
+    ("rf_batch_destroy", _int, [_vp]),
+    ("rf_batch_process", _int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("rf_batch_last_error", C.c_char_p, [_vp]),
     ("rf_set_profiling", _int, [_vp, _int]),
     ("rf_get_profile", _int, [_vp, _vp, C.POINTER(rf_profile)]),
     ("rf_sync_status", _int, [_vp, _vp]),
@@ -344,3 +348,46 @@ class Volume:
             _check(lib.rf_extract_mesh(self.h, verts.data_ptr(), cols.data_ptr(), nt, C.byref(n), _stream(stream)),
                    self.h)
         return verts[:nt], cols[:nt]
+
+
+class Batch:
+    """One frame for each of several volumes per call (rf_batch_process)."""
+
+    def __init__(self, volumes):
+        import torch
+        self.torch = torch
+        self.volumes = list(volumes)
+        lib = load()
+        arr = (C.c_void_p * len(self.volumes))(*[v.h.value for v in self.volumes])
+        self._arr = arr
+        h = C.c_void_p()
+        st = lib.rf_batch_create(arr, len(self.volumes), C.byref(h))
+        if st != RF_OK:
+            raise RFError(st, lib.rf_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def process(self, frames, T_inits, T_outs, masks=None, stream=None):
+        """frames: list of rf_frame; T_inits/T_outs: device float64 [4,4] tensors;
+        masks: optional list of device uint8 [H,W] tensors (or None entries)."""
+        n = len(self.volumes)
+        fr = (rf_frame * n)(*frames)
+        tin = (C.c_void_p * n)(*[t.data_ptr() for t in T_inits])
+        tout = (C.c_void_p * n)(*[t.data_ptr() for t in T_outs])
+        m = None
+        if masks is not None:
+            m = (C.c_void_p * n)(*[(x.data_ptr() if x is not None else None) for x in masks])
+        lib = load()
+        st = lib.rf_batch_process(self.h, fr, tin, tout, m, _stream(stream))
+        if st != RF_OK:
+            raise RFError(st, lib.rf_batch_last_error(self.h).decode())

@@ -391,3 +391,53 @@ def test_invalid_arguments(R):
     with pytest.raises(R.RFError) as e:
         vol.integrate(fr, np.eye(4))
     assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# batches of streams (one launch covers several uneven streams)
+# ---------------------------------------------------------------------------
+
+def test_batch_is_bit_identical_to_single_streams(R):
+    """Three streams of different resolution, intrinsics and voxel size: the
+    batched path gives exactly the poses, masks and volumes of the streams
+    processed alone (partial sums over fixed pixel chunks)."""
+    from synth.scenes import CAM_QVGA
+    specs = [("tiny", 0, None, 0.02), ("dynamic", 1, CAM_QVGA, 0.03), ("static", 2, None, 0.01)]
+    seqs = [make_sequence(c, sd, n_frames=4, camera=cam) for c, sd, cam, _ in specs]
+    outs = {}
+    for mode in ("single", "batch"):
+        vols = [gpu_volume(R, s.camera, vx, n_buckets=1 << 18, max_blocks=150000) for s, (_, _, _, vx) in
+                zip(seqs, specs)]
+        batch = R.Batch(vols) if mode == "batch" else None
+        T = [None] * len(seqs)
+        poses, masks = [], []
+        for i in range(4):
+            frames, tin, tout, mk = [], [], [], []
+            for k, s in enumerate(seqs):
+                d, rgb, Tgt, _ = s.frame(i)
+                frames.append(dev_frame(R, vols[k], d, rgb, s.camera))
+                tin.append(torch.as_tensor(Tgt if T[k] is None else T[k], device="cuda").contiguous())
+                tout.append(torch.empty(4, 4, dtype=torch.float64, device="cuda"))
+                mk.append(torch.empty(s.camera.height, s.camera.width, dtype=torch.uint8, device="cuda"))
+            if batch is not None:
+                batch.process(frames, tin, tout, mk)
+            else:
+                for k in range(len(seqs)):
+                    R.rf_process_frame(vols[k].h, frames[k], tin[k], tout[k], mk[k], None)
+            for v in vols:
+                v.sync()
+            T = [t.cpu().numpy() for t in tout]
+            poses.append(np.array(T))
+            masks.append([m.cpu().numpy() for m in mk])
+        outs[mode] = (np.array(poses), masks, [v.export() for v in vols])
+        if batch is not None:
+            batch.close()
+        for v in vols:
+            v.close()
+    np.testing.assert_array_equal(outs["single"][0], outs["batch"][0])
+    for ma, mb in zip(outs["single"][1], outs["batch"][1]):
+        for a, b in zip(ma, mb):
+            np.testing.assert_array_equal(a, b)
+    for sa, sb in zip(outs["single"][2], outs["batch"][2]):
+        for key in ("coords", "F", "W", "rgb", "wc"):
+            np.testing.assert_array_equal(sa[key], sb[key])
