@@ -84,8 +84,8 @@ typedef struct rf_params {
 typedef struct rf_frame {
   int height, width;
   double fx, fy, cx, cy;   /* pinhole intrinsics (Eq. 1); fx*256 and (cx+0.5)*256 are rounded to integers */
-  const uint16_t* depth;   /* device, height*width */
-  const uint8_t* rgb;      /* device, height*width*3 */
+  const uint16_t* depth;   /* height*width; device or page-locked host memory */
+  const uint8_t* rgb;      /* height*width*3; device or page-locked host memory */
 } rf_frame;
 
 /* Registration summary (written to device memory by rf_track_frame). */
@@ -132,10 +132,18 @@ rf_status rf_default_params(rf_params* p);
 rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width,
                            int max_height, rf_volume** out);
 
+/* Device bytes rf_create_volume would allocate for these arguments (the same
+ * argument checks, no allocation, no device needed): what an admission
+ * policy charges against its memory budget.  Equals rf_stats.device_bytes of
+ * the created volume. */
+rf_status rf_volume_footprint(const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width,
+                              int max_height, int64_t* bytes);
+
 /* Synchronises the device and frees everything the volume owns.  NULL is a no-op. */
 rf_status rf_destroy_volume(rf_volume* vol);
 
-/* Empties the volume (all blocks freed, frame counter 0); synchronous. */
+/* Empties the volume (all blocks freed, frame counter 0; the next frame is
+ * integrated at its T_init without tracking); synchronous. */
 rf_status rf_volume_reset(rf_volume* vol);
 
 /* Levenberg-Marquardt registration of a frame against the model (Sec. III-B):
@@ -189,7 +197,8 @@ rf_status rf_integrate_frame(rf_volume* vol, const rf_frame* frame, const double
 
 /* The whole per-frame loop (Fig. 2 / Sec. III-C): track -> mask -> track
  * without masked pixels -> integrate with that pose and mask.  The first frame
- * of a volume is integrated at *T_init_dev without tracking.  Device pointers:
+ * of an empty volume (new, reset, or imported from an empty snapshot) is
+ * integrated at *T_init_dev without tracking.  Device pointers:
  * T_init_dev (in), T_out_dev (out), mask_dev (out, nullable), info_dev (out,
  * nullable; info of the second registration).  The frame is copied into
  * volume-owned staging buffers first, so the caller may reuse its buffers once
@@ -210,19 +219,27 @@ rf_status rf_process_frame_host(rf_volume* vol, int height, int width, const dou
 /* Batches: one frame for each of n volumes (independent camera streams, any
  * mix of resolutions and voxel sizes) per call.  The two registrations of all
  * streams run as one cooperative launch each, with one group of CTAs per
- * stream sized by its pixel count (the groups never wait on each other); the
- * masks and integrations of the streams run concurrently.  A stream's result
- * is bit-identical to processing it alone with rf_process_frame (partial
- * sums are taken over fixed pixel chunks, not per CTA).
+ * tracked stream sized by its pixel count (the groups never wait on each
+ * other); the masks and integrations of the streams run concurrently.  A
+ * stream's result is bit-identical to processing it alone with
+ * rf_process_frame (partial sums are taken over fixed pixel chunks, not per
+ * CTA).
  * rf_batch_create: n <= number of SMs; volumes on the current device, each
  * at most once.  It allocates the batch's streams and events; each new batch
- * shape (frame sizes, intrinsics, which streams are on their first frame)
- * captures a graph and allocates its small descriptor buffers on first use.
+ * shape (frame sizes and intrinsics) captures a graph and allocates its small
+ * descriptor buffers on first use.
  * rf_batch_process: frames, T_init_dev, T_out_dev, mask_dev (nullable, and
  * entries nullable) are arrays of n, device pointers as in rf_process_frame.
- * Asynchronous on `stream`; kernel-detected errors go to each volume's
- * rf_sync_status.  A batch must not run concurrently with other work on its
- * volumes. */
+ * A stream whose frames[i].depth is NULL sits the call out: its volume is left
+ * unchanged, T_out_dev[i] receives T_init_dev[i], its mask is not written (its
+ * frame's size and intrinsics must still be the stream's).  A stream whose
+ * volume is empty is integrated at T_init (as rf_process_frame does).  Which
+ * streams track, start or sit out changes per call without a new capture: the
+ * call uploads one small table (pointers, modes, the CTA split) and replays
+ * the graph.  Asynchronous on `stream`; successive calls on one batch must be
+ * ordered (same stream, or synchronised by the caller); kernel-detected errors
+ * go to each volume's rf_sync_status.  A batch must not run concurrently with
+ * other work on its volumes. */
 typedef struct rf_batch rf_batch;
 rf_status rf_batch_create(rf_volume* const* vols, int n, rf_batch** out);
 rf_status rf_batch_destroy(rf_batch* batch);
@@ -246,8 +263,9 @@ rf_status rf_extract_mesh(rf_volume* vol, float* verts_dev, uint8_t* colors_dev,
 rf_status rf_volume_export(rf_volume* vol, int64_t cap_blocks, int32_t* coords, float* F, uint8_t* W,
                            uint8_t* rgb, uint8_t* wc, int64_t* n_blocks);
 
-/* Replaces the volume content with a host snapshot in the export layout.
- * Synchronous. */
+/* Replaces the volume content with a host snapshot in the export layout;
+ * with n_blocks > 0 the next frame is tracked against it (eviction to the
+ * host and back leaves a stream's results unchanged).  Synchronous. */
 rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coords, const float* F,
                            const uint8_t* W, const uint8_t* rgb, const uint8_t* wc);
 

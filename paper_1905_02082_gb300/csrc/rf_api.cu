@@ -117,6 +117,42 @@ rf_status validate_params(const rf_params* p) {
   return RF_OK;
 }
 
+rf_status check_volume_args(const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width, int max_height) {
+  rf_status s = validate_params(p);
+  if (s) return s;
+  if (n_buckets < 1 || (n_buckets & (n_buckets - 1)) != 0 || n_buckets > ((int64_t)1 << 30))
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "n_buckets must be a power of two <= 2^30");
+  if (max_blocks < 1 || max_blocks > kMaxPool) return set_error(nullptr, RF_ERR_INVALID_ARG, "max_blocks out of range");
+  if (max_width < 1 || max_height < 1 || max_width > 8192 || max_height > 8192)
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "frame size out of range");
+  return RF_OK;
+}
+
+// Every device buffer of a volume, in one list: rf_create_volume allocates
+// them, rf_volume_footprint adds up their sizes.
+template <class Alloc>
+rf_status volume_buffers(rf_volume* vol, const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width,
+                         int max_height, Alloc&& A) {
+  const size_t npix = (size_t)max_width * max_height;
+  const size_t max_chunks = (npix + 511) / 512;
+  const size_t ntiles = ((size_t)(max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
+  const size_t nslots = (size_t)n_buckets * kSlots;
+  rf_status s;
+  if ((s = A(&vol->d_hash, nslots, "hash")) || (s = A(&vol->d_vox, (size_t)max_blocks * kBV, "voxels")) ||
+      (s = A(&vol->d_W, (size_t)max_blocks * kBV, "weights")) || (s = A(&vol->d_coords, (size_t)max_blocks, "coords")) ||
+      (s = A(&vol->d_nbr, 2 * (size_t)max_blocks, "neighbour tables")) || (s = A(&vol->d_nblocks, 1, "pool")) ||
+      (s = A(&vol->d_status, 1, "status")) || (s = A(&vol->d_regbar, 2, "barrier")) ||
+      (s = A(&vol->d_partials, 2 * 29 * max_chunks + 2, "partials")) || (s = A(&vol->d_seeds, npix, "seeds")) ||
+      (s = A(&vol->d_md, npix, "mask work")) || (s = A(&vol->d_ff, (size_t)p->max_ff_sweeps + 2, "flood-fill words")) ||
+      (s = A(&vol->d_integ, 1, "integ")) || (s = A(&vol->d_tilemax, ntiles, "tiles")) ||
+      (s = A(&vol->d_cand, (size_t)p->max_candidates, "candidates")) || (s = A(&vol->d_depth, npix, "depth staging")) ||
+      (s = A(&vol->d_rgb, npix * 3, "rgb staging")) || (s = A(&vol->d_mask, npix, "mask staging")) ||
+      (s = A(&vol->d_T, 48, "poses")) || (s = A(&vol->d_info, 1, "info")) || (s = A(&vol->d_guard, 1, "guard count")))
+    return s;
+  return RF_OK;
+}
+
+
 DevParams derive(const rf_params& p) {
   DevParams d;
   d.voxel = (float)p.voxel_size;
@@ -283,11 +319,34 @@ rf_status run_frame(rf_volume* vol, const rf_frame* fr, bool first, cudaGraphExe
 // ---------------------------------------------------------------------------
 // batches: one frame for each of several volumes (independent camera streams)
 // ---------------------------------------------------------------------------
+// Per-stream, per-call part of a batch, uploaded with one copy before each
+// replay: the staging kernel copies the caller's frame and pose into the
+// volume, the output kernel copies the pose (and mask) back.
+struct BatchStage {
+  const uint16_t* depth_src;  // NULL: the stream sits this batch out
+  const uint8_t* rgb_src;
+  const double* T_src;
+  uint16_t* depth_dst;
+  uint8_t* rgb_dst;
+  double* T_dst;  // the volume's [3][16] poses
+  double* T_out;
+  uint8_t* mask_out;  // nullable
+  const uint8_t* mask_src;
+  int npix;
+  int mode;  // kModeTrack, kModeFirst or kModeIdle
+};
+
+constexpr int kModeTrack = 0;  // track, mask, track again, integrate
+constexpr int kModeFirst = 1;  // empty model: integrate at T_init (no registration CTAs)
+constexpr int kModeIdle = 2;   // no frame: empty depth, pose passed through, nothing changes
+
 struct rf_batch_graph {
-  std::vector<double> sig;  // per stream: H, W, fx, fy, cx, cy, first
+  std::vector<double> sig;  // per stream: H, W, fx, fy, cx, cy
   cudaGraphExec_t exec = nullptr;
-  RegDesc* d_desc = nullptr;  // [2][n]: first and second registration
-  int* d_cta = nullptr;       // CTA -> stream, then the n + 1 group starts
+  RegDesc* d_desc = nullptr;   // [2][n]: first and second registration
+  void* d_table = nullptr;     // [n] BatchStage, then CTA -> stream [total], then n + 1 group starts
+  std::vector<unsigned char> h_table;
+  int total_ctas = 0;
 };
 
 struct rf_batch {
@@ -301,6 +360,56 @@ struct rf_batch {
 };
 
 namespace {
+
+__device__ __forceinline__ void copy_bytes(void* dst, const void* src, size_t n, size_t tid, size_t nth) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0;
+  size_t done = 0;
+  if (vec) {
+    const size_t n16 = n / 16;
+    const uint4* s4 = static_cast<const uint4*>(src);
+    uint4* d4 = static_cast<uint4*>(dst);
+    for (size_t i = tid; i < n16; i += nth) d4[i] = __ldg(s4 + i);
+    done = n16 * 16;
+  }
+  const uint8_t* s1 = static_cast<const uint8_t*>(src);
+  uint8_t* d1 = static_cast<uint8_t*>(dst);
+  for (size_t i = done + tid; i < n; i += nth) d1[i] = s1[i];
+}
+
+__device__ __forceinline__ void zero_bytes(void* dst, size_t n, size_t tid, size_t nth) {
+  uint8_t* d1 = static_cast<uint8_t*>(dst);
+  size_t done = 0;
+  if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    uint4* d4 = static_cast<uint4*>(dst);
+    for (size_t i = tid; i < n / 16; i += nth) d4[i] = make_uint4(0, 0, 0, 0);
+    done = n / 16 * 16;
+  }
+  for (size_t i = done + tid; i < n; i += nth) d1[i] = 0;
+}
+
+// grid (x, n streams): frame and pose of every stream into its volume.
+__global__ void __launch_bounds__(256) k_batch_stage(const BatchStage* __restrict__ table) {
+  const BatchStage& b = table[blockIdx.y];
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+  if (b.mode == kModeIdle) {
+    zero_bytes(b.depth_dst, (size_t)b.npix * 2, tid, nth);
+  } else {
+    copy_bytes(b.depth_dst, b.depth_src, (size_t)b.npix * 2, tid, nth);
+    copy_bytes(b.rgb_dst, b.rgb_src, (size_t)b.npix * 3, tid, nth);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 48) {
+    const int k = threadIdx.x;
+    if (k < 16 || b.mode != kModeTrack) b.T_dst[k] = b.T_src[k & 15];
+  }
+}
+
+// grid (x, n streams): final pose (and mask) of every stream to the caller.
+__global__ void __launch_bounds__(256) k_batch_out(const BatchStage* __restrict__ table) {
+  const BatchStage& b = table[blockIdx.y];
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+  if (b.mask_out && b.mode != kModeIdle) copy_bytes(b.mask_out, b.mask_src, (size_t)b.npix, tid, nth);
+  if (blockIdx.x == 0 && threadIdx.x < 16) b.T_out[threadIdx.x] = b.T_dst[32 + threadIdx.x];
+}
 
 rf_status batch_error(rf_batch* b, rf_status s, const std::string& msg) {
   b->last_error = msg;
@@ -321,17 +430,26 @@ void join_aux(rf_batch* b, cudaStream_t cs) {
   }
 }
 
-// CTA groups of the batched registration: at least one CTA per stream, the
-// rest in proportion to the stream's pixel count (largest remainders).
+// CTA groups of the batched registration: streams of weight 0 get none, the
+// others at least one and the rest in proportion to their weight (pixel
+// count), largest remainders first.
 std::vector<int> split_ctas(const std::vector<double>& weight, int total) {
   const int n = (int)weight.size();
-  std::vector<int> cnt(n, 1);
+  std::vector<int> cnt(n, 0);
   double wsum = 0.0;
-  for (double w : weight) wsum += w;
-  const int spare = total - n;
+  int active = 0;
+  for (int i = 0; i < n; ++i)
+    if (weight[i] > 0.0) {
+      cnt[i] = 1;
+      wsum += weight[i];
+      ++active;
+    }
+  if (active == 0) return cnt;
+  const int spare = total - active;
   std::vector<std::pair<double, int>> rem;
   int given = 0;
   for (int i = 0; i < n; ++i) {
+    if (weight[i] <= 0.0) continue;
     const double share = spare * weight[i] / wsum;
     const int whole = (int)share;
     cnt[i] += whole;
@@ -341,45 +459,32 @@ std::vector<int> split_ctas(const std::vector<double>& weight, int total) {
   std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
     return x.first != y.first ? x.first > y.first : x.second < y.second;
   });
-  for (int k = 0; k < spare - given && k < n; ++k) cnt[rem[k].second]++;
+  for (int k = 0; k < spare - given && k < (int)rem.size(); ++k) cnt[rem[k].second]++;
   return cnt;
 }
 
+size_t table_bytes(int n, int total_ctas) { return sizeof(BatchStage) * n + sizeof(int) * (total_ctas + n + 1); }
+
+// Captures the batch graph for one shape.  Every stream gets the full path;
+// which streams actually track is decided per replay by the uploaded table.
 rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<double>& sig, rf_batch_graph* out) {
   const int n = (int)b->vols.size();
   std::vector<DevFrame> f(n);
-  std::vector<int> nf;  // streams past their first frame (tracked)
+  std::vector<RegDesc> desc(2 * n);
   for (int i = 0; i < n; ++i) {
+    rf_volume* v = b->vols[i];
     rf_frame staged = frames[i];
-    staged.depth = b->vols[i]->d_depth;
-    staged.rgb = b->vols[i]->d_rgb;
+    staged.depth = v->d_depth;
+    staged.rgb = v->d_rgb;
     f[i] = make_dev_frame(&staged);
-    if (b->vols[i]->frames > 0) nf.push_back(i);
+    desc[i] = make_reg_desc(v, f[i], v->d_T, nullptr, v->d_T + 16, nullptr);
+    desc[n + i] = make_reg_desc(v, f[i], v->d_T + 16, v->d_mask, v->d_T + 32, v->d_info);
   }
-  const int total_ctas = b->vols[0]->reg_grid;
-  std::vector<RegDesc> desc(2 * (nf.empty() ? 1 : nf.size()));
-  std::vector<int> cta;
-  if (!nf.empty()) {
-    std::vector<double> w;
-    for (int i : nf) {
-      rf_volume* v = b->vols[i];
-      desc[w.size()] = make_reg_desc(v, f[i], v->d_T, nullptr, v->d_T + 16, nullptr);
-      desc[nf.size() + w.size()] = make_reg_desc(v, f[i], v->d_T + 16, v->d_mask, v->d_T + 32, v->d_info);
-      w.push_back((double)frames[i].width * frames[i].height);
-    }
-    const std::vector<int> cnt = split_ctas(w, total_ctas);
-    std::vector<int> first(nf.size() + 1, 0);
-    for (size_t k = 0; k < nf.size(); ++k) {
-      first[k + 1] = first[k] + cnt[k];
-      for (int c = 0; c < cnt[k]; ++c) cta.push_back((int)k);
-    }
-    cta.insert(cta.end(), first.begin(), first.end());
-  }
+  out->total_ctas = b->vols[0]->reg_grid;
+  out->h_table.assign(table_bytes(n, out->total_ctas), 0);
   cudaError_t e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
-  if (e == cudaSuccess) e = cudaMalloc(&out->d_cta, sizeof(int) * (cta.size() + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&out->d_table, out->h_table.size());
   if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !cta.empty())
-    e = cudaMemcpy(out->d_cta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch descriptors: ") + cudaGetErrorString(e));
   std::vector<bool> prof(n);
   for (int i = 0; i < n; ++i) {
@@ -393,45 +498,33 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
   if (e != cudaSuccess) {
     s = batch_error(b, RF_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
   } else {
-    const int nt = (int)nf.size();
-    const RegDesc* d1 = out->d_desc;
-    const RegDesc* d2 = out->d_desc + nt;
-    const int* cta_stream = out->d_cta;
-    const int* group_first = out->d_cta + total_ctas;
-    if (nt > 0) {
-      for (int i : nf) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
-      s = launch_register_batch(b->vols[nf[0]], d1, cta_stream, group_first, total_ctas, cs);
-      // residual seeds and erosion: concurrent; flood fills (cooperative): one at a time
-      fork_aux(b, cs);
-      for (int k = 0; k < nt && !s; ++k) {
-        rf_volume* v = b->vols[nf[k]];
-        s = launch_mask_pre(v, f[nf[k]], v->d_T + 16, b->aux[k % rf_batch::kAux]);
-      }
-      join_aux(b, cs);
-      for (int k = 0; k < nt && !s; ++k) s = launch_mask_ff(b->vols[nf[k]], f[nf[k]], cs);
-      fork_aux(b, cs);
-      for (int k = 0; k < nt && !s; ++k) {
-        rf_volume* v = b->vols[nf[k]];
-        s = launch_mask_post(v, f[nf[k]], v->d_mask, b->aux[k % rf_batch::kAux]);
-      }
-      join_aux(b, cs);
-      for (int i : nf) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
-      if (!s) s = launch_register_batch(b->vols[nf[0]], d2, cta_stream, group_first, total_ctas, cs);
-    }
+    const BatchStage* table = static_cast<const BatchStage*>(out->d_table);
+    const int* cta_stream = reinterpret_cast<const int*>(table + n);
+    const int* group_first = cta_stream + out->total_ctas;
+    int max_npix = 1;
+    for (int i = 0; i < n; ++i) max_npix = std::max(max_npix, f[i].H * f[i].W);
+    const dim3 copy_grid((unsigned)std::min((max_npix * 3 / 16 + 255) / 256, 64), (unsigned)n);
+    k_batch_stage<<<copy_grid, 256, 0, cs>>>(table);
+    for (int i = 0; i < n; ++i) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
+    s = launch_register_batch(b->vols[0], out->d_desc, cta_stream, group_first, out->total_ctas, cs);
+    // residual seeds and erosion: concurrent; flood fills (cooperative): one at a time
+    fork_aux(b, cs);
+    for (int i = 0; i < n && !s; ++i)
+      s = launch_mask_pre(b->vols[i], f[i], b->vols[i]->d_T + 16, b->aux[i % rf_batch::kAux]);
+    join_aux(b, cs);
+    for (int i = 0; i < n && !s; ++i) s = launch_mask_ff(b->vols[i], f[i], cs);
+    fork_aux(b, cs);
+    for (int i = 0; i < n && !s; ++i)
+      s = launch_mask_post(b->vols[i], f[i], b->vols[i]->d_mask, b->aux[i % rf_batch::kAux]);
+    join_aux(b, cs);
+    for (int i = 0; i < n; ++i) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
+    if (!s) s = launch_register_batch(b->vols[0], out->d_desc + n, cta_stream, group_first, out->total_ctas, cs);
     // integrations: concurrent
     fork_aux(b, cs);
-    for (int i = 0; i < n && !s; ++i) {
-      rf_volume* v = b->vols[i];
-      cudaStream_t a = b->aux[i % rf_batch::kAux];
-      if (v->frames == 0) {
-        cudaMemsetAsync(v->d_mask, 0, (size_t)f[i].H * f[i].W, a);
-        s = launch_integrate(v, f[i], v->d_T, nullptr, a);
-        cudaMemcpyAsync(v->d_T + 32, v->d_T, 16 * sizeof(double), cudaMemcpyDeviceToDevice, a);
-      } else {
-        s = launch_integrate(v, f[i], v->d_T + 32, v->d_mask, a);
-      }
-    }
+    for (int i = 0; i < n && !s; ++i)
+      s = launch_integrate(b->vols[i], f[i], b->vols[i]->d_T + 32, b->vols[i]->d_mask, b->aux[i % rf_batch::kAux]);
     join_aux(b, cs);
+    k_batch_out<<<dim3(copy_grid.x, n), 256, 0, cs>>>(table);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (!s && ce != cudaSuccess) s = batch_error(b, RF_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(ce));
@@ -519,13 +612,8 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
   if (!out) return set_error(nullptr, RF_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!p) return set_error(nullptr, RF_ERR_INVALID_ARG, "params is NULL");
-  rf_status s = validate_params(p);
+  rf_status s = check_volume_args(p, n_buckets, max_blocks, max_width, max_height);
   if (s) return s;
-  if (n_buckets < 1 || (n_buckets & (n_buckets - 1)) != 0 || n_buckets > ((int64_t)1 << 30))
-    return set_error(nullptr, RF_ERR_INVALID_ARG, "n_buckets must be a power of two <= 2^30");
-  if (max_blocks < 1 || max_blocks > kMaxPool) return set_error(nullptr, RF_ERR_INVALID_ARG, "max_blocks out of range");
-  if (max_width < 1 || max_height < 1 || max_width > 8192 || max_height > 8192)
-    return set_error(nullptr, RF_ERR_INVALID_ARG, "frame size out of range");
   rf_volume* vol = new rf_volume();
   vol->p = *p;
   vol->dp = derive(*p);
@@ -549,21 +637,8 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
     delete vol;
     return s;
   }
-  const size_t ntiles = ((size_t)(max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
-  const size_t nslots = (size_t)n_buckets * kSlots;
-  if ((s = dalloc(vol, &vol->d_hash, nslots, "hash")) || (s = dalloc(vol, &vol->d_vox, (size_t)max_blocks * kBV, "voxels")) ||
-      (s = dalloc(vol, &vol->d_W, (size_t)max_blocks * kBV, "weights")) ||
-      (s = dalloc(vol, &vol->d_coords, (size_t)max_blocks, "coords")) ||
-      (s = dalloc(vol, &vol->d_nbr, 2 * (size_t)max_blocks, "neighbour tables")) || (s = dalloc(vol, &vol->d_nblocks, 1, "pool")) ||
-      (s = dalloc(vol, &vol->d_status, 1, "status")) || (s = dalloc(vol, &vol->d_regbar, 2, "barrier")) ||
-      (s = dalloc(vol, &vol->d_partials, (size_t)2 * 29 * vol->max_chunks + 2, "partials")) ||
-      (s = dalloc(vol, &vol->d_seeds, npix, "seeds")) || (s = dalloc(vol, &vol->d_md, npix, "mask work")) ||
-      (s = dalloc(vol, &vol->d_ff, (size_t)p->max_ff_sweeps + 2, "flood-fill words")) ||
-      (s = dalloc(vol, &vol->d_integ, 1, "integ")) || (s = dalloc(vol, &vol->d_tilemax, ntiles, "tiles")) ||
-      (s = dalloc(vol, &vol->d_cand, (size_t)p->max_candidates, "candidates")) ||
-      (s = dalloc(vol, &vol->d_depth, npix, "depth staging")) || (s = dalloc(vol, &vol->d_rgb, npix * 3, "rgb staging")) ||
-      (s = dalloc(vol, &vol->d_mask, npix, "mask staging")) || (s = dalloc(vol, &vol->d_T, 48, "poses")) ||
-      (s = dalloc(vol, &vol->d_info, 1, "info")) || (s = dalloc(vol, &vol->d_guard, 1, "guard count"))) {
+  if ((s = volume_buffers(vol, p, n_buckets, max_blocks, max_width, max_height,
+                          [&](auto** ptr, size_t count, const char* what) { return dalloc(vol, ptr, count, what); }))) {
     g_create_error = vol->last_error;
     rf_destroy_volume(vol);
     return s;
@@ -595,12 +670,30 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
   return RF_OK;
 }
 
+rf_status rf_volume_footprint(const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width, int max_height,
+                              int64_t* bytes) {
+  if (!bytes) return set_error(nullptr, RF_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = 0;
+  if (!p) return set_error(nullptr, RF_ERR_INVALID_ARG, "params is NULL");
+  rf_status s = check_volume_args(p, n_buckets, max_blocks, max_width, max_height);
+  if (s) return s;
+  rf_volume shape;
+  size_t total = 0;
+  volume_buffers(&shape, p, n_buckets, max_blocks, max_width, max_height, [&](auto** ptr, size_t count, const char*) {
+    total += (count ? count : 1) * sizeof(**ptr);
+    return RF_OK;
+  });
+  *bytes = (int64_t)total;
+  return RF_OK;
+}
+
 rf_status rf_volume_reset(rf_volume* vol) {
   if (!vol) return RF_ERR_INVALID_ARG;
   rf_status s = clear_model(vol, 0);
   if (!s) s = check_cuda(vol, cudaMemset(vol->d_status, 0, sizeof(unsigned)), "status reset");
   if (!s) s = check_cuda(vol, cudaDeviceSynchronize(), "reset sync");
   vol->frames = 0;
+  vol->has_model = false;
   return s;
 }
 
@@ -634,14 +727,14 @@ rf_status rf_process_frame(rf_volume* vol, const rf_frame* frame, const double* 
   if (!T_init_dev || !T_out_dev) return set_error(vol, RF_ERR_INVALID_ARG, "NULL pose");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t npix = (size_t)frame->height * frame->width;
-  const bool first = vol->frames == 0;
+  const bool first = !vol->has_model;
   cudaGraphExec_t exec = nullptr;
   rf_status s = vol->use_graphs ? frame_graph(vol, frame, first, &exec) : RF_OK;
   if (s) return s;
-  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_depth, frame->depth, npix * 2, cudaMemcpyDeviceToDevice, st),
+  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_depth, frame->depth, npix * 2, cudaMemcpyDefault, st),
                       "depth staging")))
     return s;
-  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_rgb, frame->rgb, npix * 3, cudaMemcpyDeviceToDevice, st),
+  if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_rgb, frame->rgb, npix * 3, cudaMemcpyDefault, st),
                       "rgb staging")))
     return s;
   if ((s = check_cuda(vol, cudaMemcpyAsync(vol->d_T, T_init_dev, 16 * sizeof(double), cudaMemcpyDeviceToDevice, st),
@@ -661,6 +754,7 @@ rf_status rf_process_frame(rf_volume* vol, const rf_frame* frame, const double* 
     if (s) return s;
   }
   vol->frames++;
+  vol->has_model = true;
   return RF_OK;
 }
 
@@ -674,7 +768,7 @@ rf_status rf_process_frame_host(rf_volume* vol, int height, int width, const dou
   if (!frame_ok(vol, &fr)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t npix = (size_t)height * width;
-  const bool first = vol->frames == 0;
+  const bool first = !vol->has_model;
   cudaGraphExec_t exec = nullptr;
   rf_status s = vol->use_graphs ? frame_graph(vol, &fr, first, &exec) : RF_OK;
   if (s) return s;
@@ -690,6 +784,7 @@ rf_status rf_process_frame_host(rf_volume* vol, int height, int width, const dou
                                    "mask D2H")))
     return s;
   vol->frames++;
+  vol->has_model = true;
   return rf_sync_status(vol, stream);
 }
 
@@ -797,6 +892,7 @@ rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coor
   if (!s) s = launch_nbr_fixup(vol, nullptr, 0, nullptr);
   if (!s) s = check_cuda(vol, cudaDeviceSynchronize(), "import sync");
   if (s) return s;
+  vol->has_model = true;  // the next frame is tracked against the imported model
   return rf_sync_status(vol, nullptr);
 }
 
@@ -896,7 +992,7 @@ rf_status rf_batch_destroy(rf_batch* b) {
   for (auto& g : b->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.d_desc) cudaFree(g.d_desc);
-    if (g.d_cta) cudaFree(g.d_cta);
+    if (g.d_table) cudaFree(g.d_table);
   }
   for (int k = 0; k < rf_batch::kAux; ++k) {
     if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
@@ -914,12 +1010,19 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
   if (!b || !frames || !T_init_dev || !T_out_dev) return RF_ERR_INVALID_ARG;
   const int n = (int)b->vols.size();
   std::vector<double> sig;
+  std::vector<int> mode(n);
   for (int i = 0; i < n; ++i) {
-    if (!frame_ok(b->vols[i], &frames[i])) return batch_error(b, RF_ERR_INVALID_ARG, "invalid frame in batch");
-    if (!T_init_dev[i] || !T_out_dev[i]) return batch_error(b, RF_ERR_INVALID_ARG, "NULL pose in batch");
+    rf_volume* v = b->vols[i];
     const rf_frame& fr = frames[i];
-    sig.insert(sig.end(), {(double)fr.height, (double)fr.width, fr.fx, fr.fy, fr.cx, fr.cy,
-                           b->vols[i]->frames == 0 ? 1.0 : 0.0});
+    mode[i] = fr.depth == nullptr ? kModeIdle : (v->has_model ? kModeTrack : kModeFirst);
+    rf_frame shape = fr;
+    if (mode[i] == kModeIdle) {  // shape checks only
+      shape.depth = v->d_depth;
+      shape.rgb = v->d_rgb;
+    }
+    if (!frame_ok(v, &shape)) return batch_error(b, RF_ERR_INVALID_ARG, "invalid frame in batch");
+    if (!T_init_dev[i] || !T_out_dev[i]) return batch_error(b, RF_ERR_INVALID_ARG, "NULL pose in batch");
+    sig.insert(sig.end(), {(double)fr.height, (double)fr.width, fr.fx, fr.fy, fr.cx, fr.cy});
   }
   rf_batch_graph* g = nullptr;
   for (auto& x : b->graphs)
@@ -931,31 +1034,49 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
     if (s != RF_OK) {
       if (g->exec) cudaGraphExecDestroy(g->exec);
       if (g->d_desc) cudaFree(g->d_desc);
-      if (g->d_cta) cudaFree(g->d_cta);
+      if (g->d_table) cudaFree(g->d_table);
       b->graphs.pop_back();
       return s;
     }
   }
+  // per-call table: staging pointers and modes, then the registration CTA map
+  BatchStage* tab = reinterpret_cast<BatchStage*>(g->h_table.data());
+  int* cta_stream = reinterpret_cast<int*>(tab + n);
+  int* group_first = cta_stream + g->total_ctas;
+  std::vector<double> w(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    rf_volume* v = b->vols[i];
+    BatchStage& t = tab[i];
+    t.depth_src = frames[i].depth;
+    t.rgb_src = frames[i].rgb;
+    t.T_src = T_init_dev[i];
+    t.depth_dst = v->d_depth;
+    t.rgb_dst = v->d_rgb;
+    t.T_dst = v->d_T;
+    t.T_out = T_out_dev[i];
+    t.mask_out = mask_dev ? mask_dev[i] : nullptr;
+    t.mask_src = v->d_mask;
+    t.npix = frames[i].height * frames[i].width;
+    t.mode = mode[i];
+    if (mode[i] == kModeTrack) w[i] = (double)t.npix;
+  }
+  const std::vector<int> cnt = split_ctas(w, g->total_ctas);
+  int c = 0;
+  for (int i = 0; i < n; ++i) {
+    group_first[i] = c;
+    for (int k = 0; k < cnt[i]; ++k) cta_stream[c++] = i;
+  }
+  group_first[n] = c;
+  for (; c < g->total_ctas; ++c) cta_stream[c] = -1;
   cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(g->d_table, g->h_table.data(), g->h_table.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, st);
+  if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   for (int i = 0; i < n; ++i) {
-    rf_volume* v = b->vols[i];
-    const size_t npix = (size_t)frames[i].height * frames[i].width;
-    cudaMemcpyAsync(v->d_depth, frames[i].depth, npix * 2, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(v->d_rgb, frames[i].rgb, npix * 3, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(v->d_T, T_init_dev[i], 16 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (mode[i] == kModeIdle) continue;
+    b->vols[i]->frames++;
+    b->vols[i]->has_model = true;
   }
-  cudaError_t e = cudaGraphLaunch(g->exec, st);
-  if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
-  for (int i = 0; i < n; ++i) {
-    rf_volume* v = b->vols[i];
-    cudaMemcpyAsync(T_out_dev[i], v->d_T + 32, 16 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    if (mask_dev && mask_dev[i])
-      cudaMemcpyAsync(mask_dev[i], v->d_mask, (size_t)frames[i].height * frames[i].width, cudaMemcpyDeviceToDevice,
-                      st);
-    v->frames++;
-  }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch copies: ") + cudaGetErrorString(e));
   return RF_OK;
 }
 

@@ -513,12 +513,15 @@ __global__ void __launch_bounds__(kRegThreads, 1) k_register(RegDesc d) { regist
 
 // Several independent registrations in one cooperative launch: CTA b runs
 // stream cta_stream[b] as member b - first[s] of a group of first[s+1] -
-// first[s] CTAs.  Groups never wait on each other.
+// first[s] CTAs.  Groups never wait on each other.  A CTA mapped to stream
+// -1 has no work (streams that sit a batch out, or are on their first frame,
+// get no CTAs; the map is rewritten per batch without re-capturing the graph).
 __global__ void __launch_bounds__(kRegThreads, 1)
     k_register_batch(const RegDesc* __restrict__ descs, const int* __restrict__ cta_stream,
                      const int* __restrict__ first) {
   __shared__ RegDesc sd;
   const int s = cta_stream[blockIdx.x];
+  if (s < 0) return;
   if (threadIdx.x == 0) sd = descs[s];
   __syncthreads();
   register_body(sd, blockIdx.x - first[s], first[s + 1] - first[s]);

@@ -65,5 +65,6 @@ struct rf_volume {
   std::vector<rf_graph_entry> graphs;
   bool use_graphs = true;
   int64_t frames = 0;
+  bool has_model = false;  // false: the next frame is integrated at its T_init without tracking
   std::string last_error;
 };

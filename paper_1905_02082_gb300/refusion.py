@@ -64,6 +64,7 @@ _vp, _i64, _int = C.c_void_p, C.c_int64, C.c_int
 SIGNATURES = [
     ("rf_default_params", _int, [C.POINTER(rf_params)]),
     ("rf_create_volume", _int, [C.POINTER(rf_params), _i64, _i64, _int, _int, C.POINTER(_vp)]),
+    ("rf_volume_footprint", _int, [C.POINTER(rf_params), _i64, _i64, _int, _int, C.POINTER(_i64)]),
     ("rf_destroy_volume", _int, [_vp]),
     ("rf_volume_reset", _int, [_vp]),
     ("rf_track_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp, _vp, _vp]),
@@ -150,16 +151,32 @@ def rf_create_volume(params: rf_params, n_buckets: int, max_blocks: int, max_wid
     return h
 
 
+def rf_volume_footprint(params: rf_params, n_buckets: int, max_blocks: int, max_width: int, max_height: int) -> int:
+    out = C.c_int64()
+    lib = load()
+    st = lib.rf_volume_footprint(C.byref(params), n_buckets, max_blocks, max_width, max_height, C.byref(out))
+    if st != RF_OK:
+        raise RFError(st, lib.rf_last_error(None).decode())
+    return out.value
+
+
 def rf_destroy_volume(h):
     _check(load().rf_destroy_volume(h))
 
 
 def make_frame(depth, rgb, fx, fy, cx, cy) -> rf_frame:
-    """rf_frame over device tensors depth [H,W] uint16 and rgb [H,W,3] uint8."""
+    """rf_frame over tensors depth [H,W] uint16 and rgb [H,W,3] uint8, on the
+    device or in page-locked host memory."""
     H, W = int(depth.shape[0]), int(depth.shape[1])
     assert tuple(rgb.shape) == (H, W, 3)
-    assert depth.is_contiguous() and rgb.is_contiguous() and depth.is_cuda and rgb.is_cuda
+    assert depth.is_contiguous() and rgb.is_contiguous()
+    assert (depth.is_cuda or depth.is_pinned()) and (rgb.is_cuda or rgb.is_pinned())
     return rf_frame(H, W, float(fx), float(fy), float(cx), float(cy), depth.data_ptr(), rgb.data_ptr())
+
+
+def idle_frame(height, width, fx, fy, cx, cy) -> rf_frame:
+    """rf_frame without images: in rf_batch_process the stream sits the call out."""
+    return rf_frame(int(height), int(width), float(fx), float(fy), float(cx), float(cy), None, None)
 
 
 def rf_track_frame(h, frame: rf_frame, T_init, mask, T_out, info=None, stream=None):

@@ -513,7 +513,8 @@ class Sequence:
     per (seed, index), independent of access order)."""
 
     def __init__(self, config: str, seed: int = 0, n_frames: Optional[int] = None,
-                 camera: Optional[Camera] = None, noise: Optional[str] = None, movers: Optional[int] = None):
+                 camera: Optional[Camera] = None, noise: Optional[str] = None, movers: Optional[int] = None,
+                 coverage_scale: int = 1):
         cfg = dict(CONFIGS[config])
         self.config = config
         self.seed = seed
@@ -531,14 +532,20 @@ class Sequence:
             for _attempt in range(20):
                 self.scene.prims = list(base)
                 add_movers(self.scene, rng, n_mov)
-                cov = np.mean([self._render(i)[2].mean() for i in (0, min(self.n_frames - 1, 15))])
+                cov = np.mean([self._render(i, coverage_scale)[2].mean() for i in (0, min(self.n_frames - 1, 15))])
                 if 0.10 <= cov <= 0.40:
                     break
         self.n_movers = n_mov
 
-    def _render(self, i):
+    def _render(self, i, scale: int = 1):
+        """Ray cast of frame i; scale > 1 renders a 1/scale-resolution image
+        (used only to measure the movers' pixel coverage quickly)."""
         prims = self.scene.at_time(i / FPS)
-        return render(prims, self.camera, self.poses[i], self.scene.light)
+        cam = self.camera
+        if scale > 1:
+            cam = Camera(cam.width // scale, cam.height // scale, cam.fx / scale, cam.fy / scale,
+                         (cam.cx + 0.5) / scale - 0.5, (cam.cy + 0.5) / scale - 0.5)
+        return render(prims, cam, self.poses[i], self.scene.light)
 
     def frame(self, i: int):
         """(depth uint16 [H,W] mm, rgb uint8 [H,W,3], T_gt 4x4, static_mask bool [H,W])."""

@@ -85,3 +85,21 @@ def test_argument_errors_are_reported_on_the_host(lib_path):
     assert lib.rf_destroy_volume(None) == 0
     assert lib.rf_track_frame(None, None, None, None, None, None, None) == 1
     assert lib.rf_status_string(3) == b"hash table full"
+
+
+def test_volume_footprint_without_a_device(lib_path):
+    """rf_volume_footprint needs no GPU and charges exactly the per-block and
+    per-bucket storage: a block is 512 voxels x (8 B value/colour word + 1 B
+    weight) + its coordinates (16 B) + its neighbour table (32 B); a bucket is
+    4 slots x 8 B."""
+    import paper_1905_02082_gb300.refusion as R
+    p = R.rf_default_params()
+    base = R.rf_volume_footprint(p, 1 << 12, 1000, 640, 480)
+    assert R.rf_volume_footprint(p, 1 << 12, 1001, 640, 480) - base == 512 * 9 + 16 + 32
+    assert R.rf_volume_footprint(p, 1 << 13, 1000, 640, 480) - base == (1 << 12) * 4 * 8
+    # per-pixel scratch grows with the frame bound
+    assert R.rf_volume_footprint(p, 1 << 12, 1000, 1280, 720) > base
+    with pytest.raises(R.RFError):
+        R.rf_volume_footprint(p, 1000, 1000, 640, 480)  # buckets not a power of two
+    with pytest.raises(R.RFError):
+        R.rf_volume_footprint(p, 1 << 12, 0, 640, 480)

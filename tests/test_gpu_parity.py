@@ -441,3 +441,89 @@ def test_batch_is_bit_identical_to_single_streams(R):
     for sa, sb in zip(outs["single"][2], outs["batch"][2]):
         for key in ("coords", "F", "W", "rgb", "wc"):
             np.testing.assert_array_equal(sa[key], sb[key])
+
+
+@pytest.mark.gpu
+def test_batch_streams_join_sit_out_and_evict(R):
+    """Streams that join a running batch (first frame), sit calls out (no
+    frame) and are evicted to the host and re-imported give exactly the poses,
+    masks and volumes of the same frames processed alone, one stream after the
+    other, with rf_process_frame."""
+    from synth.scenes import CAM_QVGA
+    specs = [("static", 3, None, 0.02), ("dynamic", 4, CAM_QVGA, 0.03), ("tiny", 5, None, 0.02)]
+    seqs = [make_sequence(c, sd, n_frames=5, camera=cam) for c, sd, cam, _ in specs]
+    # per step: which frame each stream gets (None: sits out); stream 2 is
+    # exported after step 1 and imported back before step 4
+    plan = [(0, None, 0), (1, 0, 1), (2, 1, None), (3, None, None), (4, 2, 2), (None, 3, 3)]
+    evict_after, restore_before = 1, 4
+
+    def frame_of(k, i):
+        d, rgb, Tgt, _ = seqs[k].frame(i)
+        return d, rgb, Tgt
+
+    # alone
+    alone = []
+    for k, s in enumerate(seqs):
+        v = gpu_volume(R, s.camera, specs[k][3], n_buckets=1 << 18, max_blocks=150000)
+        T, poses, masks = None, [], []
+        for i in sorted({p[k] for p in plan if p[k] is not None}):
+            d, rgb, Tgt = frame_of(k, i)
+            fr = dev_frame(R, v, d, rgb, s.camera)
+            tin = torch.as_tensor(Tgt if T is None else T, device="cuda").contiguous()
+            tout = torch.empty(4, 4, dtype=torch.float64, device="cuda")
+            mk = torch.empty(s.camera.height, s.camera.width, dtype=torch.uint8, device="cuda")
+            R.rf_process_frame(v.h, fr, tin, tout, mk, None)
+            v.sync()
+            T = tout.cpu().numpy()
+            poses.append(T)
+            masks.append(mk.cpu().numpy())
+        alone.append((poses, masks, v.export()))
+        v.close()
+
+    # mixed
+    vols = [gpu_volume(R, s.camera, specs[k][3], n_buckets=1 << 18, max_blocks=150000) for k, s in enumerate(seqs)]
+    batch = R.Batch(vols)
+    T = [None] * 3
+    mixed = [([], []) for _ in seqs]
+    saved = None
+    for step, p in enumerate(plan):
+        if step == restore_before:
+            vols[2].import_(saved)
+        frames, tin, tout, mk = [], [], [], []
+        for k, s in enumerate(seqs):
+            cam = s.camera
+            if p[k] is None:
+                frames.append(R.idle_frame(cam.height, cam.width, cam.fx, cam.fy, cam.cx, cam.cy))
+                start = T[k] if T[k] is not None else np.eye(4)
+            else:
+                d, rgb, Tgt = frame_of(k, p[k])
+                frames.append(dev_frame(R, vols[k], d, rgb, cam))
+                start = Tgt if T[k] is None else T[k]
+            tin.append(torch.as_tensor(start, device="cuda").contiguous())
+            tout.append(torch.full((4, 4), float("nan"), dtype=torch.float64, device="cuda"))
+            mk.append(torch.full((cam.height, cam.width), 7, dtype=torch.uint8, device="cuda"))
+        batch.process(frames, tin, tout, mk)
+        for v in vols:
+            v.sync()
+        for k in range(3):
+            out = tout[k].cpu().numpy()
+            if p[k] is None:
+                np.testing.assert_array_equal(out, tin[k].cpu().numpy())
+                assert (mk[k].cpu().numpy() == 7).all(), "a stream that sat out had its mask written"
+            else:
+                T[k] = out
+                mixed[k][0].append(out)
+                mixed[k][1].append(mk[k].cpu().numpy())
+        if step == evict_after:
+            saved = vols[2].export()
+            vols[2].reset()
+    snaps = [v.export() for v in vols]
+    batch.close()
+    for v in vols:
+        v.close()
+    for k in range(3):
+        np.testing.assert_array_equal(np.array(alone[k][0]), np.array(mixed[k][0]))
+        for a, b in zip(alone[k][1], mixed[k][1]):
+            np.testing.assert_array_equal(a, b)
+        for key in ("coords", "F", "W", "rgb", "wc"):
+            np.testing.assert_array_equal(alone[k][2][key], snaps[k][key])
