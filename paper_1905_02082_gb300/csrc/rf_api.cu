@@ -58,6 +58,7 @@ DevFrame make_dev_frame(const rf_frame* f) {
   d.amb_v = (float)(4.0 * (6e-7 * 2.0 * (f->height + std::fabs(f->cy)) + 2.5e-4));
   d.depth = f->depth;
   d.rgb = f->rgb;
+  d.gate = nullptr;
   return d;
 }
 
@@ -331,14 +332,10 @@ struct BatchStage {
   double* T_dst;  // the volume's [3][16] poses
   double* T_out;
   uint8_t* mask_out;  // nullable
-  const uint8_t* mask_src;
+  uint8_t* mask_buf;  // the volume's mask (zeroed for a first frame: nothing is masked)
   int npix;
-  int mode;  // kModeTrack, kModeFirst or kModeIdle
+  int mode;  // kModeTrack, kModeFirst or kModeIdle; the gate of the stream's kernels
 };
-
-constexpr int kModeTrack = 0;  // track, mask, track again, integrate
-constexpr int kModeFirst = 1;  // empty model: integrate at T_init (no registration CTAs)
-constexpr int kModeIdle = 2;   // no frame: empty depth, pose passed through, nothing changes
 
 struct rf_batch_graph {
   std::vector<double> sig;  // per stream: H, W, fx, fy, cx, cy
@@ -391,12 +388,11 @@ __device__ __forceinline__ void zero_bytes(void* dst, size_t n, size_t tid, size
 __global__ void __launch_bounds__(256) k_batch_stage(const BatchStage* __restrict__ table) {
   const BatchStage& b = table[blockIdx.y];
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
-  if (b.mode == kModeIdle) {
-    zero_bytes(b.depth_dst, (size_t)b.npix * 2, tid, nth);
-  } else {
+  if (b.mode != kModeIdle) {
     copy_bytes(b.depth_dst, b.depth_src, (size_t)b.npix * 2, tid, nth);
     copy_bytes(b.rgb_dst, b.rgb_src, (size_t)b.npix * 3, tid, nth);
   }
+  if (b.mode == kModeFirst) zero_bytes(b.mask_buf, (size_t)b.npix, tid, nth);
   if (blockIdx.x == 0 && threadIdx.x < 48) {
     const int k = threadIdx.x;
     if (k < 16 || b.mode != kModeTrack) b.T_dst[k] = b.T_src[k & 15];
@@ -407,7 +403,7 @@ __global__ void __launch_bounds__(256) k_batch_stage(const BatchStage* __restric
 __global__ void __launch_bounds__(256) k_batch_out(const BatchStage* __restrict__ table) {
   const BatchStage& b = table[blockIdx.y];
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
-  if (b.mask_out && b.mode != kModeIdle) copy_bytes(b.mask_out, b.mask_src, (size_t)b.npix, tid, nth);
+  if (b.mask_out && b.mode != kModeIdle) copy_bytes(b.mask_out, b.mask_buf, (size_t)b.npix, tid, nth);
   if (blockIdx.x == 0 && threadIdx.x < 16) b.T_out[threadIdx.x] = b.T_dst[32 + threadIdx.x];
 }
 
@@ -469,6 +465,11 @@ size_t table_bytes(int n, int total_ctas) { return sizeof(BatchStage) * n + size
 // which streams actually track is decided per replay by the uploaded table.
 rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<double>& sig, rf_batch_graph* out) {
   const int n = (int)b->vols.size();
+  out->total_ctas = b->vols[0]->reg_grid;
+  out->h_table.assign(table_bytes(n, out->total_ctas), 0);
+  cudaError_t e = cudaMalloc(&out->d_table, out->h_table.size());
+  if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch table: ") + cudaGetErrorString(e));
+  const void* out_table = out->d_table;
   std::vector<DevFrame> f(n);
   std::vector<RegDesc> desc(2 * n);
   for (int i = 0; i < n; ++i) {
@@ -477,13 +478,12 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     staged.depth = v->d_depth;
     staged.rgb = v->d_rgb;
     f[i] = make_dev_frame(&staged);
+    f[i].gate = reinterpret_cast<const int*>(static_cast<const char*>(out_table) + i * sizeof(BatchStage) +
+                                             offsetof(BatchStage, mode));
     desc[i] = make_reg_desc(v, f[i], v->d_T, nullptr, v->d_T + 16, nullptr);
     desc[n + i] = make_reg_desc(v, f[i], v->d_T + 16, v->d_mask, v->d_T + 32, v->d_info);
   }
-  out->total_ctas = b->vols[0]->reg_grid;
-  out->h_table.assign(table_bytes(n, out->total_ctas), 0);
-  cudaError_t e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
-  if (e == cudaSuccess) e = cudaMalloc(&out->d_table, out->h_table.size());
+  e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
   if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch descriptors: ") + cudaGetErrorString(e));
   std::vector<bool> prof(n);
@@ -1055,7 +1055,7 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
     t.T_dst = v->d_T;
     t.T_out = T_out_dev[i];
     t.mask_out = mask_dev ? mask_dev[i] : nullptr;
-    t.mask_src = v->d_mask;
+    t.mask_buf = v->d_mask;
     t.npix = frames[i].height * frames[i].width;
     t.mode = mode[i];
     if (mode[i] == kModeTrack) w[i] = (double)t.npix;

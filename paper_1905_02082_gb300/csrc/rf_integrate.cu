@@ -31,7 +31,9 @@ namespace {
 
 // Quantised pose (one entry per lane: conversions run on the FP64 pipe, so
 // they are spread over lanes) and reset of the per-frame counters.
-__global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const int* __restrict__ n_blocks) {
+__global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const int* __restrict__ n_blocks,
+                             const int* gate) {
+  if (gated_off(gate, kModeFirst)) return;
   const int a = threadIdx.x;
   if (a < 9) {
     const int i = a / 3, j = a % 3;
@@ -54,6 +56,7 @@ __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const
 
 __global__ void __launch_bounds__(256) k_tilemax(DevFrame f, DevParams p, const uint8_t* __restrict__ mask,
                                                  int* __restrict__ tilemax, IntegState* st, int tiles_x) {
+  if (gated_off(f.gate, kModeFirst)) return;
   const int tile = blockIdx.x;
   const int u = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
   const int v = (tile / tiles_x) * kTile + (threadIdx.x / kTile);
@@ -84,6 +87,7 @@ constexpr long long kMaxSearchBlocks = 1ll << 28;
 // min(max valid depth + tau, d_max), over the pixel rectangle.  Float math on
 // 8 lanes (one frustum corner each); the 2-voxel margin covers its rounding.
 __global__ void k_integ_aabb(const double* __restrict__ T, DevFrame f, DevParams p, IntegState* st) {
+  if (gated_off(f.gate, kModeFirst)) return;
   const int lane = threadIdx.x;
   const int max_um = st->max_um;
   if (max_um < 0) {
@@ -190,6 +194,7 @@ __device__ bool cull_keep(int bx, int by, int bz, const DevFrame& f, const DevPa
 __global__ void __launch_bounds__(256) k_cull(DevFrame f, DevParams p, IntegState* st, const int* __restrict__ tilemax,
                                               int tiles_x, int tiles_y, int4* __restrict__ cand, long long max_cand,
                                               unsigned* status) {
+  if (gated_off(f.gate, kModeFirst)) return;
   __shared__ IntegState s;
   if (threadIdx.x == 0) s = *st;
   __syncthreads();
@@ -337,6 +342,7 @@ __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame 
   __shared__ int s_px[kIntegWarps][kVPL][32];    // pixel index | band << 31, or -1
   __shared__ float s_x[kIntegWarps][kVPL][32];   // update value
   __shared__ long long A[9], tq[3];              // quantised pose
+  if (gated_off(f.gate, kModeFirst)) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int(*spx)[32] = s_px[wid];
   float(*sx)[32] = s_x[wid];
@@ -492,7 +498,9 @@ __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame 
 // the pools of its 7 positive neighbours, and each existing negative
 // neighbour gets the new block in the matching slot.  Runs after the
 // integration (the hash is complete and read-only here).
-__global__ void __launch_bounds__(256) k_nbr_fixup(DevVol v, const int* __restrict__ lo_ptr, int lo_value) {
+__global__ void __launch_bounds__(256) k_nbr_fixup(DevVol v, const int* __restrict__ lo_ptr, int lo_value,
+                                                   const int* gate) {
+  if (gated_off(gate, kModeFirst)) return;
   const int lo = lo_ptr ? *lo_ptr : lo_value;
   const int hi = min(*(volatile int*)v.n_blocks, v.max_blocks);
   int* flat = reinterpret_cast<int*>(v.nbr);
@@ -515,14 +523,14 @@ __global__ void __launch_bounds__(256) k_nbr_fixup(DevVol v, const int* __restri
 
 }  // namespace
 
-rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st) {
-  k_nbr_fixup<<<vol->sm_count * 2, 256, 0, st>>>(vol->dv, lo_ptr, lo);
+rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st, const int* gate) {
+  k_nbr_fixup<<<vol->sm_count * 2, 256, 0, st>>>(vol->dv, lo_ptr, lo, gate);
   return check_cuda(vol, cudaGetLastError(), "neighbour table launch");
 }
 
 rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st) {
   const int tiles_x = (f.W + kTile - 1) / kTile, tiles_y = (f.H + kTile - 1) / kTile;
-  k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks);
+  k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks, f.gate);
   k_tilemax<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x);
   k_integ_aabb<<<1, 32, 0, st>>>(T, f, vol->dp, vol->d_integ);
   k_cull<<<vol->sm_count * 8, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
@@ -533,7 +541,7 @@ rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, c
   prof_record(vol, EV_KERNEL1, st);
   rf_status s = check_cuda(vol, cudaGetLastError(), "integrate launch");
   if (s != RF_OK) return s;
-  return launch_nbr_fixup(vol, &vol->d_integ->pool_before, 0, st);
+  return launch_nbr_fixup(vol, &vol->d_integ->pool_before, 0, st, f.gate);
 }
 
 }  // namespace rf

@@ -79,7 +79,20 @@ struct DevFrame {
   float amb_u, amb_v;
   const uint16_t* depth;
   const uint8_t* rgb;
+  // batches only: the stream's per-call mode (kMode*), read by every mask and
+  // integration kernel of the stream; nullptr outside batches
+  const int* gate;
 };
+
+// Per-call mode of a stream in a batch.  Track: the whole path.  First (empty
+// volume): no registration or mask, integration at T_init.  Idle (no frame):
+// nothing runs.
+constexpr int kModeTrack = 0, kModeFirst = 1, kModeIdle = 2;
+
+// True when a gated kernel has no work: the stream's mode is above max_mode.
+__device__ __forceinline__ bool gated_off(const int* gate, int max_mode) {
+  return gate != nullptr && __ldg(gate) > max_mode;
+}
 
 struct LMConst {
   double lambda0, eps_t, eps_r;
@@ -275,5 +288,5 @@ rf_status launch_mask_pre(rf_volume* vol, const DevFrame& f, const double* T, cu
 rf_status launch_mask_ff(rf_volume* vol, const DevFrame& f, cudaStream_t st);
 rf_status launch_mask_post(rf_volume* vol, const DevFrame& f, uint8_t* mask_out, cudaStream_t st);
 // neighbour tables of the blocks allocated since *lo_ptr (or since lo when lo_ptr is null)
-rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st);
+rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st, const int* gate = nullptr);
 }  // namespace rf

@@ -90,6 +90,7 @@ __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevPar
 
 __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p, const double* __restrict__ T,
                                                uint8_t* __restrict__ seeds, unsigned* guard_count) {
+  if (gated_off(f.gate, kModeTrack)) return;
   // pose and threshold converted once per CTA (conversions use the FP64 pipe)
   __shared__ float sR[12];
   __shared__ double s_t64;
@@ -164,7 +165,9 @@ __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p
   seeds[idx] = seed;
 }
 
-__global__ void __launch_bounds__(256) k_erode(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ mr) {
+__global__ void __launch_bounds__(256) k_erode(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ mr,
+                                               const int* gate) {
+  if (gated_off(gate, kModeTrack)) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= H * W) return;
   const int u = idx % W, v = idx / W;
@@ -180,7 +183,9 @@ __global__ void __launch_bounds__(256) k_erode(const uint8_t* __restrict__ in, i
   mr[idx] = all;
 }
 
-__global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ out,
+                                                const int* gate) {
+  if (gated_off(gate, kModeTrack)) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= H * W) return;
   const int u = idx % W, v = idx / W;
@@ -208,7 +213,8 @@ __device__ __forceinline__ bool ff_edge(unsigned Dsrc, unsigned Ddst, long long 
 // ff words: [0] barrier count, [1] barrier generation, [2 + s] changed in sweep s
 __global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uint16_t* __restrict__ depth, int H,
                                                            int W, long long theta_ppm, unsigned* ff, int max_sweeps,
-                                                           unsigned* status) {
+                                                           unsigned* status, const int* gate) {
+  if (gated_off(gate, kModeTrack)) return;  // uniform over the grid: before any barrier
   __shared__ uint8_t sm[kFFH + 2][kFFW + 2];
   __shared__ uint16_t sd[kFFH + 2][kFFW + 2];
   const int tiles_x = (W + kFFW - 1) / kFFW, tiles_y = (H + kFFH - 1) / kFFH;
@@ -263,7 +269,7 @@ rf_status launch_mask_pre(rf_volume* vol, const DevFrame& f, const double* T, cu
   rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_guard, 0, sizeof(unsigned), st), "guard reset");
   if (s != RF_OK) return s;
   k_seeds<<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds, vol->d_guard);
-  k_erode<<<blocks, 256, 0, st>>>(vol->d_seeds, f.H, f.W, vol->d_md);
+  k_erode<<<blocks, 256, 0, st>>>(vol->d_seeds, f.H, f.W, vol->d_md, f.gate);
   s = check_cuda(vol, cudaMemsetAsync(vol->d_ff, 0, sizeof(unsigned) * (2 + vol->p.max_ff_sweeps), st),
                  "flood-fill reset");
   if (s != RF_OK) return s;
@@ -284,13 +290,13 @@ rf_status launch_mask_ff(rf_volume* vol, const DevFrame& f, cudaStream_t st) {
   cfg.numAttrs = 1;
   return check_cuda(vol,
                     cudaLaunchKernelEx(&cfg, k_floodfill, vol->d_md, f.depth, f.H, f.W, vol->dp.theta_ppm, vol->d_ff,
-                                       vol->p.max_ff_sweeps, vol->d_status),
+                                       vol->p.max_ff_sweeps, vol->d_status, f.gate),
                     "flood-fill launch");
 }
 
 rf_status launch_mask_post(rf_volume* vol, const DevFrame& f, uint8_t* mask_out, cudaStream_t st) {
   const int n = f.H * f.W;
-  k_dilate<<<(n + 255) / 256, 256, 0, st>>>(vol->d_md, f.H, f.W, mask_out);
+  k_dilate<<<(n + 255) / 256, 256, 0, st>>>(vol->d_md, f.H, f.W, mask_out, f.gate);
   return check_cuda(vol, cudaGetLastError(), "mask launch");
 }
 
@@ -374,7 +380,7 @@ extern "C" rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* fra
   // the array keeps the previous call's contents: zero the words that count
   if ((s = check_cuda(vol, cudaMemsetAsync(ff, 0, sizeof(unsigned) * kNoAllocWords, st), "scratch clear"))) return s;
   k_seeds<<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard);
-  k_erode<<<blocks, 256, 0, st>>>(seeds, f.H, f.W, md);
+  k_erode<<<blocks, 256, 0, st>>>(seeds, f.H, f.W, md, nullptr);
   const int ntiles = ((f.W + kFFW - 1) / kFFW) * ((f.H + kFFH - 1) / kFFH);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ntiles < vol->ff_grid ? ntiles : vol->ff_grid);
@@ -386,9 +392,9 @@ extern "C" rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* fra
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if ((s = check_cuda(vol, cudaLaunchKernelEx(&cfg, k_floodfill, md, f.depth, f.H, f.W, vol->dp.theta_ppm, ff,
-                                              sweeps, vol->d_status),
+                                              sweeps, vol->d_status, (const int*)nullptr),
                       "flood-fill launch")))
     return s;
-  k_dilate<<<blocks, 256, 0, st>>>(md, f.H, f.W, mask_dev);
+  k_dilate<<<blocks, 256, 0, st>>>(md, f.H, f.W, mask_dev, nullptr);
   return check_cuda(vol, cudaGetLastError(), "mask launch");
 }
