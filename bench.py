@@ -132,17 +132,21 @@ def run_serving(R, plan, clips, args):
            "workload": "32 streams, 320x240/640x480/1280x720 cycled, voxel 1-4 cm (>=2 cm at 1280x720), 0-3 movers, "
                        "Poisson arrivals; each stream plays a rendered clip back and forth; frames in page-locked "
                        "host memory, read by the batch's staging kernel"}
-    for mode in ("batch", "per_stream"):
+    # the batched FP16 form, the batched FP32 form, and the plain per-stream FP32 path
+    for name, mode, storage in (("batch_fp16", "batch", R.STORAGE_FP16), ("batch_fp32", "batch", R.STORAGE_FP32),
+                                ("per_stream_fp32", "per_stream", R.STORAGE_FP32)):
+        run_specs = [StreamSpec(**{**sp.__dict__, "storage": storage}) for sp in specs]
         eng = ServingEngine(SERVING_BUDGET, mode=mode)
         # warm-up: one short pass so that graph capture and first-touch costs stay out of the timed run
-        warm = [StreamSpec(**{**sp.__dict__, "order": sp.order[:3], "arrivals": [0.0, 0.001, 0.002]}) for sp in specs]
+        warm = [StreamSpec(**{**sp.__dict__, "order": sp.order[:3], "arrivals": [0.0, 0.001, 0.002]})
+                for sp in run_specs]
         eng.run(warm, time_limit=120.0)
         eng.results.clear()
-        res = eng.run(specs, time_limit=300.0)
+        res = eng.run(run_specs, time_limit=300.0)
         summ = summarize(res)
         summ["peak_bytes"] = eng.stats["peak_bytes"]
         summ["batches"] = eng.stats["batches"]
-        out[mode] = summ
+        out[name] = summ
         eng.close()
     return out
 
@@ -284,14 +288,45 @@ def cpu_baseline(n_frames: int = 4):
                       f"({1.0 / full:.3f} frames/s)"}
 
 
-def run_batch(R, frames, K, cam, dev, stream, flush, args):
+def run_single(R, frames, K, cam, dev, stream, flush, args, storage):
+    """The single-stream loop of the headline number in another storage mode
+    (same frames, same timing rules): frames/s and per-frame p50/p99."""
+    import torch
+    d_depth = [torch.from_numpy(f[0].astype(np.int32)).to(dev).to(torch.uint16).contiguous() for f in frames]
+    d_rgb = [torch.from_numpy(f[1]).to(dev).contiguous() for f in frames]
+    vol = R.Volume(n_buckets=N_BUCKETS, max_blocks=MAX_BLOCKS, max_width=cam.width, max_height=cam.height,
+                   voxel_size=VOXEL, trunc=TAU, storage=storage)
+    T = torch.as_tensor(frames[0][2], device=dev).contiguous()
+    Tn = torch.empty_like(T)
+    for i in range(args.warmup):
+        R.rf_process_frame(vol.h, vol.frame(d_depth[i], d_rgb[i], K), T, Tn, None, None, stream)
+        T, Tn = Tn, T
+    vol.sync()
+    ms = []
+    for k in range(args.steps):
+        i = args.warmup + k
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        R.rf_process_frame(vol.h, vol.frame(d_depth[i], d_rgb[i], K), T, Tn, None, None, stream)
+        b.record(stream)
+        T, Tn = Tn, T
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    vol.sync()
+    vol.close()
+    return {"storage": "fp16" if storage else "fp32", "frames_per_s": len(ms) / (sum(ms) / 1000.0),
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}}
+
+
+def run_batch(R, frames, K, cam, dev, stream, flush, args, storage=0):
     """S streams (one volume each, the same rendered sequence) processed in
     lockstep batches through rf_batch_process: aggregate frames/s and the
     per-batch latency (every frame of a batch completes at the batch's end)."""
     import torch
     S = args.batch_streams
     vols = [R.Volume(n_buckets=1 << 18, max_blocks=60_000, max_width=cam.width, max_height=cam.height,
-                     voxel_size=VOXEL, trunc=TAU) for _ in range(S)]
+                     voxel_size=VOXEL, trunc=TAU, storage=storage) for _ in range(S)]
     batch = R.Batch(vols)
     n = min(len(frames), args.warmup + args.batch_steps)
     d_depth = [torch.from_numpy(f[0].astype(np.int32)).to(dev).to(torch.uint16).contiguous() for f in frames[:n]]
@@ -322,7 +357,8 @@ def run_batch(R, frames, K, cam, dev, stream, flush, args):
     batch.close()
     for v in vols:
         v.close()
-    return {"streams": S, "workload": "static room 640x480 per stream (one volume each, voxel 1 cm)",
+    return {"streams": S, "storage": "fp16" if storage else "fp32",
+            "workload": "static room 640x480 per stream (one volume each, voxel 1 cm)",
             "frames_per_s": S * len(ms) / (sum(ms) / 1000.0), "batches": len(ms),
             "batch_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                          "mean": statistics.mean(ms)},
@@ -476,8 +512,11 @@ def main():
     # neighbour tables (6)
     launches_per_frame = 2 + 4 + 6
     batch = None
+    batch_fp16 = None
     if args.batch_streams > 0:
         batch = run_batch(R, frames, K, cam, dev, stream, flush, args)
+        batch_fp16 = run_batch(R, frames, K, cam, dev, stream, flush, args, storage=R.STORAGE_FP16)
+    single_fp16 = run_single(R, frames, K, cam, dev, stream, flush, args, storage=R.STORAGE_FP16)
     serving = run_serving(R, splan, clips, args) if splan else None
 
     if rank == 0:
@@ -509,6 +548,8 @@ def main():
                      "candidates": statistics.mean(p.candidates for p in profs), "blocks": st.n_blocks,
                      "guard_pixels": statistics.mean(p.guard_pixels for p in profs)},
             "batch": batch,
+            "batch_fp16": batch_fp16,
+            "single_fp16": single_fp16,
             "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,

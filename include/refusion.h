@@ -78,7 +78,20 @@ typedef struct rf_params {
   int lm_min_valid;    /* an evaluation with fewer valid pixels is rejected */
   int max_ff_sweeps;   /* bound on flood-fill sweeps (RF_ERR_NOT_CONVERGED beyond) */
   int64_t max_candidates; /* capacity of the per-frame frustum block candidate list */
+  int storage;         /* voxel storage: RF_STORAGE_FP32 (default) or RF_STORAGE_FP16 (compact) */
 } rf_params;
+
+/* Voxel storage modes.  FP32: SDF as float, weights and colour as uint8 (9 B
+ * per voxel).  FP16 (the precision form): SDF as FP16 of F/tau, the SDF
+ * weight and an 8-bit intensity (round(254 I), Sec. III-B) in one 4-byte
+ * tracking word, colour and colour weight in a 4-byte colour word (8 B per
+ * voxel); tracking reads 4 B per trilinear corner and free-space carving
+ * rewrites 4 B per voxel.  Per-pixel maths and reductions are FP32 and the
+ * LM solve FP64 in both modes; hash indexing and the mask's decisions stay
+ * exact (on the values stored).  rf_volume_export returns F = FP16 value x
+ * tau (float multiply); rf_volume_import rounds F / tau to FP16 (nearest). */
+#define RF_STORAGE_FP32 0
+#define RF_STORAGE_FP16 1
 
 /* One RGB-D frame in device memory (row-major, rows of exactly `width`). */
 typedef struct rf_frame {

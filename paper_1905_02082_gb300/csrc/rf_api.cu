@@ -10,6 +10,7 @@
 #include <cstring>
 #include <vector>
 
+#include "rf_half.hpp"
 #include "rf_volume.hpp"
 
 namespace rf {
@@ -115,6 +116,8 @@ rf_status validate_params(const rf_params* p) {
     return set_error(nullptr, RF_ERR_INVALID_ARG, "max_ff_sweeps");
   if (p->max_candidates < 1 || p->max_candidates > (int64_t)1 << 28)
     return set_error(nullptr, RF_ERR_INVALID_ARG, "max_candidates");
+  if (p->storage != RF_STORAGE_FP32 && p->storage != RF_STORAGE_FP16)
+    return set_error(nullptr, RF_ERR_INVALID_ARG, "storage must be RF_STORAGE_FP32 or RF_STORAGE_FP16");
   return RF_OK;
 }
 
@@ -140,7 +143,8 @@ rf_status volume_buffers(rf_volume* vol, const rf_params* p, int64_t n_buckets, 
   const size_t nslots = (size_t)n_buckets * kSlots;
   rf_status s;
   if ((s = A(&vol->d_hash, nslots, "hash")) || (s = A(&vol->d_vox, (size_t)max_blocks * kBV, "voxels")) ||
-      (s = A(&vol->d_W, (size_t)max_blocks * kBV, "weights")) || (s = A(&vol->d_coords, (size_t)max_blocks, "coords")) ||
+      (s = A(&vol->d_W, p->storage == RF_STORAGE_FP32 ? (size_t)max_blocks * kBV : 1, "weights")) ||
+      (s = A(&vol->d_coords, (size_t)max_blocks, "coords")) ||
       (s = A(&vol->d_nbr, 2 * (size_t)max_blocks, "neighbour tables")) || (s = A(&vol->d_nblocks, 1, "pool")) ||
       (s = A(&vol->d_status, 1, "status")) || (s = A(&vol->d_regbar, 2, "barrier")) ||
       (s = A(&vol->d_partials, 2 * 29 * max_chunks + 2, "partials")) || (s = A(&vol->d_seeds, npix, "seeds")) ||
@@ -178,6 +182,8 @@ DevParams derive(const rf_params& p) {
   d.tau_tick = llround(p.trunc * 1e6 * 1024.0);
   d.w_max = p.w_max;
   d.theta_ppm = llround(p.theta * 1e6);
+  d.storage = p.storage;
+  d.inv_tau = (float)(1.0 / p.trunc);
   return d;
 }
 
@@ -571,6 +577,7 @@ rf_status rf_default_params(rf_params* p) {
   p->lm_min_valid = 10;
   p->max_ff_sweeps = 4096;
   p->max_candidates = (int64_t)1 << 21;
+  p->storage = RF_STORAGE_FP32;
   return RF_OK;
 }
 
@@ -824,27 +831,51 @@ rf_status rf_volume_export(rf_volume* vol, int64_t cap_blocks, int32_t* coords, 
     if (c[a].y != c[b].y) return c[a].y < c[b].y;
     return c[a].x < c[b].x;
   });
-  std::vector<uint2> vx(kBV);
-  std::vector<uint8_t> w(kBV);
-  for (size_t n = 0; n < order.size(); ++n) {
-    const int pool = order[n];
-    if ((s = check_cuda(vol, cudaMemcpy(vx.data(), vol->d_vox + (size_t)pool * kBV, sizeof(uint2) * kBV,
-                                        cudaMemcpyDeviceToHost), "export voxels")) ||
-        (s = check_cuda(vol, cudaMemcpy(w.data(), vol->d_W + (size_t)pool * kBV, kBV, cudaMemcpyDeviceToHost),
-                        "export weights")))
+  // pools in chunks, each copied in one piece; unpacked into sorted positions
+  std::vector<int64_t> pos(nb, -1);
+  for (size_t n = 0; n < order.size(); ++n) pos[order[n]] = (int64_t)n;
+  const bool fp16 = vol->p.storage == RF_STORAGE_FP16;
+  const float tau = vol->dp.tau;
+  const int kChunk = 8192;
+  std::vector<uint2> vx((size_t)std::min(nb, kChunk) * kBV);
+  std::vector<uint8_t> w(fp16 ? 1 : (size_t)std::min(nb, kChunk) * kBV);
+  for (int c0 = 0; c0 < nb; c0 += kChunk) {
+    const int cn = std::min(kChunk, nb - c0);
+    if ((s = check_cuda(vol, cudaMemcpy(vx.data(), vol->d_vox + (size_t)c0 * kBV, sizeof(uint2) * kBV * cn,
+                                        cudaMemcpyDeviceToHost), "export voxels")))
       return s;
-    coords[n * 3 + 0] = c[pool].x;
-    coords[n * 3 + 1] = c[pool].y;
-    coords[n * 3 + 2] = c[pool].z;
-    for (int i = 0; i < kBV; ++i) {
-      float f;
-      std::memcpy(&f, &vx[i].x, 4);
-      F[n * kBV + i] = w[i] ? f : 0.0f;
-      W[n * kBV + i] = w[i];
-      rgb[(n * kBV + i) * 3 + 0] = (uint8_t)(vx[i].y & 255u);
-      rgb[(n * kBV + i) * 3 + 1] = (uint8_t)((vx[i].y >> 8) & 255u);
-      rgb[(n * kBV + i) * 3 + 2] = (uint8_t)((vx[i].y >> 16) & 255u);
-      wc[n * kBV + i] = (uint8_t)(vx[i].y >> 24);
+    if (!fp16 && (s = check_cuda(vol, cudaMemcpy(w.data(), vol->d_W + (size_t)c0 * kBV, (size_t)kBV * cn,
+                                                 cudaMemcpyDeviceToHost), "export weights")))
+      return s;
+    for (int pl = c0; pl < c0 + cn; ++pl) {
+      const int64_t n = pos[pl];
+      if (n < 0) continue;
+      coords[n * 3 + 0] = c[pl].x;
+      coords[n * 3 + 1] = c[pl].y;
+      coords[n * 3 + 2] = c[pl].z;
+      const uint2* bv = vx.data() + (size_t)(pl - c0) * kBV;
+      const unsigned* trk = reinterpret_cast<const unsigned*>(bv);
+      for (int i = 0; i < kBV; ++i) {
+        const size_t k = (size_t)n * kBV + i;
+        unsigned colour;
+        if (fp16) {
+          const unsigned t = trk[i];
+          W[k] = (uint8_t)(t >> 24);
+          F[k] = W[k] ? half_bits_to_float((uint16_t)(t & 0xFFFFu)) * tau : 0.0f;
+          colour = trk[kBV + i];
+        } else {
+          float f;
+          std::memcpy(&f, &bv[i].x, 4);
+          const uint8_t wi = w[(size_t)(pl - c0) * kBV + i];
+          W[k] = wi;
+          F[k] = wi ? f : 0.0f;
+          colour = bv[i].y;
+        }
+        rgb[k * 3 + 0] = (uint8_t)(colour & 255u);
+        rgb[k * 3 + 1] = (uint8_t)((colour >> 8) & 255u);
+        rgb[k * 3 + 2] = (uint8_t)((colour >> 16) & 255u);
+        wc[k] = (uint8_t)(colour >> 24);
+      }
     }
   }
   return RF_OK;
@@ -858,23 +889,39 @@ rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coor
   rf_status s = rf_volume_reset(vol);
   if (s) return s;
   if (n_blocks == 0) return RF_OK;
+  const bool fp16 = vol->p.storage == RF_STORAGE_FP16;
+  const float tau = vol->dp.tau;
   std::vector<uint2> vx((size_t)n_blocks * kBV);
   std::vector<int4> c(n_blocks);
   for (int64_t n = 0; n < n_blocks; ++n) {
     c[n] = make_int4(coords[n * 3], coords[n * 3 + 1], coords[n * 3 + 2], 0);
+    unsigned* trk = reinterpret_cast<unsigned*>(vx.data() + (size_t)n * kBV);
     for (int i = 0; i < kBV; ++i) {
       const size_t k = (size_t)n * kBV + i;
-      float f = W[k] ? F[k] : std::nanf("");
-      unsigned bits;
-      std::memcpy(&bits, &f, 4);
-      if (W[k] == 0) bits = 0x7fc00000u;
-      vx[k] = make_uint2(bits, (unsigned)rgb[k * 3] | ((unsigned)rgb[k * 3 + 1] << 8) | ((unsigned)rgb[k * 3 + 2] << 16) |
-                                   ((unsigned)wc[k] << 24));
+      const unsigned colour = (unsigned)rgb[k * 3] | ((unsigned)rgb[k * 3 + 1] << 8) |
+                              ((unsigned)rgb[k * 3 + 2] << 16) | ((unsigned)wc[k] << 24);
+      if (fp16) {
+        unsigned t = kTrkEmpty;
+        if (W[k]) {
+          const unsigned sI = 2126u * rgb[k * 3] + 7152u * rgb[k * 3 + 1] + 722u * rgb[k * 3 + 2];
+          const unsigned i8 = wc[k] ? (254u * sI + 1275000u) / 2550000u : 255u;
+          t = (unsigned)float_to_half_bits(F[k] / tau) | (i8 << 16) | ((unsigned)W[k] << 24);
+        }
+        trk[i] = t;
+        trk[kBV + i] = colour;
+      } else {
+        float f = W[k] ? F[k] : std::nanf("");
+        unsigned bits;
+        std::memcpy(&bits, &f, 4);
+        if (W[k] == 0) bits = 0x7fc00000u;
+        vx[k] = make_uint2(bits, colour);
+      }
     }
   }
   s = check_cuda(vol, cudaMemcpy(vol->d_vox, vx.data(), sizeof(uint2) * vx.size(), cudaMemcpyHostToDevice),
                  "import voxels");
-  if (!s) s = check_cuda(vol, cudaMemcpy(vol->d_W, W, (size_t)n_blocks * kBV, cudaMemcpyHostToDevice), "import weights");
+  if (!s && !fp16)
+    s = check_cuda(vol, cudaMemcpy(vol->d_W, W, (size_t)n_blocks * kBV, cudaMemcpyHostToDevice), "import weights");
   // block coordinates go through the candidate buffer (no allocation), in chunks
   const int64_t chunk = vol->p.max_candidates;
   for (int64_t base = 0; !s && base < n_blocks; base += chunk) {
@@ -966,6 +1013,8 @@ rf_status rf_batch_create(rf_volume* const* vols, int n, rf_batch** out) {
     if (vols[i]->device != dev) return set_error(nullptr, RF_ERR_INVALID_ARG, "volumes on different devices");
     for (int j = 0; j < i; ++j)
       if (vols[j] == vols[i]) return set_error(nullptr, RF_ERR_INVALID_ARG, "a volume appears twice in a batch");
+    if (vols[i]->p.storage != vols[0]->p.storage)
+      return set_error(nullptr, RF_ERR_INVALID_ARG, "volumes of one batch must share the storage mode");
   }
   if (n > vols[0]->reg_grid)
     return set_error(nullptr, RF_ERR_INVALID_ARG, "rf_batch_create: at most %d streams per batch on this device",

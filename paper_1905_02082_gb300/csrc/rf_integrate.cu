@@ -328,6 +328,25 @@ constexpr int kIntegThreads = 128;  // 4 warps; one warp integrates one block at
 constexpr int kIntegWarps = kIntegThreads / 32;
 constexpr int kVPL = kBV / 32;       // 16 voxels per lane: voxel lane + 32 j
 
+// Colour running average of one band voxel (Sec. III-A, reading: RGB8 kept
+// rounded half up, own weight Wc): (Wc C + c) / (Wc + 1) per channel as an
+// exact integer quotient from a float reciprocal, corrected one step either way.
+__device__ __forceinline__ unsigned colour_update(unsigned word, const uint8_t* c, int w_max) {
+  const unsigned wc = word >> 24;
+  const unsigned den = 2 * (wc + 1);
+  const float rden = __frcp_rn((float)den);
+  unsigned out = 0;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    const unsigned num = 2 * (wc * ((word >> (8 * ch)) & 255u) + __ldg(c + ch)) + wc + 1;
+    unsigned q = (unsigned)((float)num * rden);
+    if (q * den > num) q -= 1;
+    else if ((q + 1) * den <= num) q += 1;
+    out |= q << (8 * ch);
+  }
+  return out | (min(wc + 1, (unsigned)w_max) << 24);
+}
+
 // One warp per candidate block (static round-robin over all warps): no CTA
 // barriers.  Lane l owns voxels (x, y, z) = (l & 7, (l >> 3) + 4 (j & 1), j >> 1),
 // j = 0..15, whose exact camera coordinates follow from the block's by int64
@@ -336,6 +355,7 @@ constexpr int kVPL = kBV / 32;       // 16 voxels per lane: voxel lane + 32 j
 // a time and the exact truncation tests, (3) hash lookup (first bucket
 // prefetched by lanes 0-3) or insert, (4) read-modify-write of the updated
 // voxels.  Per-voxel values are staged in shared memory, not registers.
+template <int ST>
 __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame f, DevParams p,
                                                              const uint8_t* __restrict__ mask, IntegState* st,
                                                              const int4* __restrict__ cand, long long max_cand) {
@@ -442,50 +462,69 @@ __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame 
     if (pool < 0) continue;
     my_new += (lane == 0 && fresh) ? 1u : 0u;
     my_updated += __popc(passbits);
-    uint2* vb = v.vox + (size_t)pool * kBV + lane;
-    uint8_t* wb = v.W + (size_t)pool * kBV + lane;
-    // 4) read-modify-write
+    if constexpr (ST == RF_STORAGE_FP32) {
+      uint2* vb = v.vox + (size_t)pool * kBV + lane;
+      uint8_t* wb = v.W + (size_t)pool * kBV + lane;
+      // 4) read-modify-write
 #pragma unroll 4
-    for (int j = 0; j < kVPL; ++j) {
-      const bool pass = (passbits >> j) & 1u;
-      uint2 w;
-      unsigned W;
-      if (fresh) {
-        w = make_uint2(nan_bits, 0u);
-        W = 0;
-      } else {
-        if (!pass) continue;
-        w = vb[32 * j];
-        W = wb[32 * j];
-      }
-      if (pass) {
-        const float F = __uint_as_float(w.x);
-        const float x = sx[j][lane];
-        const int px = spx[j][lane];
-        const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
-        w.x = __float_as_uint(Fn);
-        if (px < 0) {  // inside the band: colour too
-          const uint8_t* c = f.rgb + 3 * (size_t)(px & 0x7fffffff);
-          const unsigned wc = w.y >> 24;
-          const unsigned den = 2 * (wc + 1);
-          const float rden = __frcp_rn((float)den);
-          unsigned out = 0;
-#pragma unroll
-          for (int ch = 0; ch < 3; ++ch) {
-            // round half up of (wc C + c) / (wc + 1): exact integer quotient
-            // from a float reciprocal, corrected by one step either way
-            const unsigned num = 2 * (wc * ((w.y >> (8 * ch)) & 255u) + __ldg(c + ch)) + wc + 1;
-            unsigned q = (unsigned)((float)num * rden);
-            if (q * den > num) q -= 1;
-            else if ((q + 1) * den <= num) q += 1;
-            out |= q << (8 * ch);
-          }
-          w.y = out | (min(wc + 1, (unsigned)p.w_max) << 24);
+      for (int j = 0; j < kVPL; ++j) {
+        const bool pass = (passbits >> j) & 1u;
+        uint2 w;
+        unsigned W;
+        if (fresh) {
+          w = make_uint2(nan_bits, 0u);
+          W = 0;
+        } else {
+          if (!pass) continue;
+          w = vb[32 * j];
+          W = wb[32 * j];
         }
-        W = min(W + 1, (unsigned)p.w_max);
+        if (pass) {
+          const float F = __uint_as_float(w.x);
+          const float x = sx[j][lane];
+          const int px = spx[j][lane];
+          const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
+          w.x = __float_as_uint(Fn);
+          if (px < 0) w.y = colour_update(w.y, f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);  // band
+          W = min(W + 1, (unsigned)p.w_max);
+        }
+        vb[32 * j] = w;
+        wb[32 * j] = (uint8_t)W;
       }
-      vb[32 * j] = w;
-      wb[32 * j] = (uint8_t)W;
+    } else {
+      // FP16 storage: the tracking word always, the colour word inside the band
+      unsigned* tb = trk_words_rw(v, pool) + lane;
+      unsigned* cb = tb + kBV;
+#pragma unroll 4
+      for (int j = 0; j < kVPL; ++j) {
+        const bool pass = (passbits >> j) & 1u;
+        unsigned t;
+        if (fresh) {
+          t = kTrkEmpty;
+        } else {
+          if (!pass) continue;
+          t = tb[32 * j];
+        }
+        unsigned col = 0u;
+        bool col_written = fresh;
+        if (pass) {
+          const unsigned W = t >> 24;
+          const float x = sx[j][lane];
+          const int px = spx[j][lane];
+          const float F = __half2float(__ushort_as_half((unsigned short)(t & 0xFFFFu))) * p.tau;
+          const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
+          const unsigned h = (unsigned)__half_as_ushort(__float2half_rn(Fn * p.inv_tau));
+          unsigned i8 = (t >> 16) & 255u;
+          if (px < 0) {  // band: colour, and the intensity derived from it
+            col = colour_update(fresh ? 0u : cb[32 * j], f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);
+            col_written = true;
+            i8 = rgb_i8(col);
+          }
+          t = h | (i8 << 16) | (min(W + 1, (unsigned)p.w_max) << 24);
+        }
+        tb[32 * j] = t;
+        if (col_written) cb[32 * j] = col;
+      }
     }
   }
   my_updated = __reduce_add_sync(0xffffffffu, my_updated);
@@ -536,8 +575,12 @@ rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, c
   k_cull<<<vol->sm_count * 8, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
                                             vol->p.max_candidates, vol->d_status);
   prof_record(vol, EV_KERNEL0, st);
-  k_integrate<<<vol->sm_count * 16, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ, vol->d_cand,
-                                                           vol->p.max_candidates);
+  if (vol->p.storage == RF_STORAGE_FP16)
+    k_integrate<RF_STORAGE_FP16><<<vol->sm_count * 16, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
+                                                                             vol->d_cand, vol->p.max_candidates);
+  else
+    k_integrate<RF_STORAGE_FP32><<<vol->sm_count * 16, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
+                                                                             vol->d_cand, vol->p.max_candidates);
   prof_record(vol, EV_KERNEL1, st);
   rf_status s = check_cuda(vol, cudaGetLastError(), "integrate launch");
   if (s != RF_OK) return s;

@@ -16,6 +16,7 @@
 // 64-bit CAS publishes key and value together.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,6 +65,8 @@ struct DevParams {
   long long v_um, du_um, dmin_um, dmax_um, znear_tick, dmax_tick, tau_tick;
   int w_max;
   long long theta_ppm;
+  int storage;    // voxel storage mode (0: FP32, 1: compact FP16)
+  float inv_tau;  // 1 / tau (FP16 encoding of F / tau)
 };
 
 // One frame in device memory plus its intrinsics in the three forms used:
@@ -183,6 +186,39 @@ __device__ __forceinline__ float rgb_intensity_raw(unsigned c) {
   // two 16x8-bit dot products: (2126, 7152) . (R, G) + (722, 0) . (B, byte 3)
   const unsigned s = __dp2a_hi(722u, c, __dp2a_lo(2126u | (7152u << 16), c, 0u));
   return (float)s;
+}
+
+// ---------------------------------------------------------------------------
+// Voxel storage.  Mode 0 (FP32): per voxel a uint2 {F float bits (NaN when
+// W = 0), R | G<<8 | B<<16 | Wc<<24} plus W in the uint8 array (9 B).
+// Mode 1 (compact FP16): the block's 512 uint2 slots hold 512 tracking words
+// followed by 512 colour words (8 B per voxel, no W array):
+//   tracking word = F16(F / tau) (NaN when W = 0) | I8 << 16 | W << 24,
+//   colour word   = R | G<<8 | B<<16 | Wc<<24,
+// I8 = round(254 I) of the voxel's colour (Sec. III-B intensity), 255 when
+// Wc = 0: tracking gathers 4 bytes per corner and free-space carving
+// rewrites 4 bytes per voxel.
+// ---------------------------------------------------------------------------
+constexpr unsigned kTrkEmpty = 0x00FF7E00u;  // F16 NaN, I8 = 255, W = 0
+constexpr float kI8Scale = 1.0f / 254.0f;
+
+__device__ __forceinline__ const unsigned* trk_words(const DevVol& v, int pool) {
+  return reinterpret_cast<const unsigned*>(v.vox + (size_t)pool * kBV);
+}
+__device__ __forceinline__ unsigned* trk_words_rw(const DevVol& v, int pool) {
+  return reinterpret_cast<unsigned*>(v.vox + (size_t)pool * kBV);
+}
+
+// SDF of a tracking word, in metres: exactly F16 -> float, times tau (one
+// float multiply, the value rf_volume_export returns).
+__device__ __forceinline__ float trk_sdf(unsigned w, float tau) {
+  return __fmul_rn(__half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu))), tau);
+}
+
+// I8 of an RGB8 colour: round half up of 254 (2126 R + 7152 G + 722 B) / 2550000.
+__device__ __forceinline__ unsigned rgb_i8(unsigned c) {
+  const unsigned s = __dp2a_hi(722u, c & 0x00FFFFFFu, __dp2a_lo(2126u | (7152u << 16), c, 0u));
+  return (254u * s + 1275000u) / 2550000u;
 }
 
 __device__ __forceinline__ bool pixel_valid(const DevParams& p, unsigned raw) {

@@ -30,17 +30,23 @@ __device__ __forceinline__ double lerp_rn(double a, double b, double t) {
 }
 
 // Fetches the 8 corner SDF values of the cell with lattice origin k; false if
-// any corner is missing or unobserved.
-__device__ __forceinline__ bool corners_of(const DevVol& v, int kx, int ky, int kz, float F[8]) {
+// any corner is missing or unobserved.  FP16 storage: the stored value F16 x
+// tau (one float multiply, exactly what rf_volume_export returns).
+template <int ST>
+__device__ __forceinline__ bool corners_of(const DevVol& v, const DevParams& p, int kx, int ky, int kz, float F[8]) {
   const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
   if (pool < 0) return false;
   const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
+  auto value = [&](int pl, int i) -> float {
+    if constexpr (ST == RF_STORAGE_FP32) return __uint_as_float(__ldg(&v.vox[(size_t)pl * kBV + i].x));
+    else return trk_sdf(__ldg(trk_words(v, pl) + i), p.tau);
+  };
   if (lx < 7 && ly < 7 && lz < 7) {  // all 8 corners in one block
-    const uint2* base = v.vox + (size_t)pool * kBV + lx + 8 * ly + 64 * lz;
+    const int base = lx + 8 * ly + 64 * lz;
     const int off[8] = {0, 1, 8, 9, 64, 65, 72, 73};
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      F[n] = __uint_as_float(__ldg(&base[off[n]].x));
+      F[n] = value(pool, base + off[n]);
       if (F[n] != F[n]) return false;
     }
     return true;
@@ -52,13 +58,14 @@ __device__ __forceinline__ bool corners_of(const DevVol& v, int kx, int ky, int 
     const int ix = lx + (n & 1), iy = ly + ((n >> 1) & 1), iz = lz + ((n >> 2) & 1);
     const int pn = nb[(ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3)];
     if (pn < 0) return false;
-    F[n] = __uint_as_float(__ldg(&v.vox[(size_t)pn * kBV + (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7)].x));
+    F[n] = value(pn, (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
     if (F[n] != F[n]) return false;
   }
   return true;
 }
 
 // FP64 residual in the fixed evaluation order; r < 0 when the lookup is invalid.
+template <int ST>
 __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevParams& p, const double* T, int u, int vv,
                                 unsigned raw) {
   const double D = __ddiv_rn((double)raw, p.depth_scale_d);
@@ -80,7 +87,7 @@ __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevPar
   }
   if (abs(k[0]) > 8 * kMaxCoord || abs(k[1]) > 8 * kMaxCoord || abs(k[2]) > 8 * kMaxCoord) return -1.0;
   float F[8];
-  if (!corners_of(v, k[0], k[1], k[2], F)) return -1.0;
+  if (!corners_of<ST>(v, p, k[0], k[1], k[2], F)) return -1.0;
   const double c00 = lerp_rn(F[0], F[1], fr[0]), c10 = lerp_rn(F[2], F[3], fr[0]);
   const double c01 = lerp_rn(F[4], F[5], fr[0]), c11 = lerp_rn(F[6], F[7], fr[0]);
   const double c0 = lerp_rn(c00, c10, fr[1]), c1 = lerp_rn(c01, c11, fr[1]);
@@ -88,6 +95,7 @@ __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevPar
   return __dmul_rn(V, V);
 }
 
+template <int ST>
 __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p, const double* __restrict__ T,
                                                uint8_t* __restrict__ seeds, unsigned* guard_count) {
   if (gated_off(f.gate, kModeTrack)) return;
@@ -135,7 +143,7 @@ __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p
     }
     if (!ambiguous) {
       float F[8];
-      if (corners_of(v, k[0], k[1], k[2], F)) {
+      if (corners_of<ST>(v, p, k[0], k[1], k[2], F)) {
         const float c00 = F[0] * (1.0f - fr[0]) + F[1] * fr[0], c10 = F[2] * (1.0f - fr[0]) + F[3] * fr[0];
         const float c01 = F[4] * (1.0f - fr[0]) + F[5] * fr[0], c11 = F[6] * (1.0f - fr[0]) + F[7] * fr[0];
         const float c0 = c00 * (1.0f - fr[1]) + c10 * fr[1], c1 = c01 * (1.0f - fr[1]) + c11 * fr[1];
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p
       // an unambiguous cell with a missing corner is invalid in FP64 too: no seed
     }
     if (ambiguous) {
-      const double r64 = residual_fp64(v, f, p, T, u, vv, raw);
+      const double r64 = residual_fp64<ST>(v, f, p, T, u, vv, raw);
       seed = (r64 >= 0.0 && r64 > t64) ? 1 : 0;
       if (guard_count) atomicAdd(guard_count, 1u);
     }
@@ -268,7 +276,10 @@ rf_status launch_mask_pre(rf_volume* vol, const DevFrame& f, const double* T, cu
   const int blocks = (n + 255) / 256;
   rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_guard, 0, sizeof(unsigned), st), "guard reset");
   if (s != RF_OK) return s;
-  k_seeds<<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds, vol->d_guard);
+  if (vol->p.storage == RF_STORAGE_FP16)
+    k_seeds<RF_STORAGE_FP16><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds, vol->d_guard);
+  else
+    k_seeds<RF_STORAGE_FP32><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds, vol->d_guard);
   k_erode<<<blocks, 256, 0, st>>>(vol->d_seeds, f.H, f.W, vol->d_md, f.gate);
   s = check_cuda(vol, cudaMemsetAsync(vol->d_ff, 0, sizeof(unsigned) * (2 + vol->p.max_ff_sweeps), st),
                  "flood-fill reset");
@@ -379,7 +390,10 @@ extern "C" rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* fra
   const int blocks = (n + 255) / 256;
   // the array keeps the previous call's contents: zero the words that count
   if ((s = check_cuda(vol, cudaMemsetAsync(ff, 0, sizeof(unsigned) * kNoAllocWords, st), "scratch clear"))) return s;
-  k_seeds<<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard);
+  if (vol->p.storage == RF_STORAGE_FP16)
+    k_seeds<RF_STORAGE_FP16><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard);
+  else
+    k_seeds<RF_STORAGE_FP32><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard);
   k_erode<<<blocks, 256, 0, st>>>(seeds, f.H, f.W, md, nullptr);
   const int ntiles = ((f.W + kFFW - 1) / kFFW) * ((f.H + kFFH - 1) / kFFH);
   cudaLaunchConfig_t cfg = {};

@@ -84,7 +84,8 @@ __device__ int tet_tris(const Cell& c, const int tv[4], float* vout, uint8_t* co
   return 2;
 }
 
-__global__ void __launch_bounds__(256) k_mesh(DevVol v, float voxel, int pass, unsigned long long* counter,
+template <int ST>
+__global__ void __launch_bounds__(256) k_mesh(DevVol v, float voxel, float tau, int pass, unsigned long long* counter,
                                               float* verts, uint8_t* colors, long long cap) {
   const int pool = blockIdx.x;
   const int4 bc = v.coords[pool];
@@ -106,10 +107,17 @@ __global__ void __launch_bounds__(256) k_mesh(DevVol v, float voxel, int pass, u
       const int nbi = (xx >> 3) + 2 * (yy >> 3) + 4 * (zz >> 3);
       const int p = nb[nbi];
       if (p < 0) { ok = false; break; }
-      const uint2 w = v.vox[(size_t)p * kBV + (xx & 7) + 8 * (yy & 7) + 64 * (zz & 7)];
-      c.F[n] = __uint_as_float(w.x);
+      const int i = (xx & 7) + 8 * (yy & 7) + 64 * (zz & 7);
+      if constexpr (ST == RF_STORAGE_FP32) {
+        const uint2 w = v.vox[(size_t)p * kBV + i];
+        c.F[n] = __uint_as_float(w.x);
+        c.C[n] = w.y;
+      } else {
+        const unsigned* tw = trk_words(v, p);
+        c.F[n] = trk_sdf(tw[i], tau);
+        c.C[n] = tw[kBV + i];
+      }
       if (c.F[n] != c.F[n]) { ok = false; break; }
-      c.C[n] = w.y;
       c.P[n][0] = (float)(bc.x * 8 + xx) * voxel;
       c.P[n][1] = (float)(bc.y * 8 + yy) * voxel;
       c.P[n][2] = (float)(bc.z * 8 + zz) * voxel;
@@ -153,7 +161,10 @@ rf_status run_mesh(rf_volume* vol, float* verts, uint8_t* colors, int64_t cap, i
     if (pass == 1 && (verts == nullptr || colors == nullptr)) break;
     s = check_cuda(vol, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st), "mesh reset");
     if (s != RF_OK) return s;
-    if (nb > 0) k_mesh<<<nb, 256, 0, st>>>(vol->dv, vol->dp.voxel, pass, d_cnt, verts, colors, cap);
+    if (nb > 0 && vol->p.storage == RF_STORAGE_FP16)
+      k_mesh<RF_STORAGE_FP16><<<nb, 256, 0, st>>>(vol->dv, vol->dp.voxel, vol->dp.tau, pass, d_cnt, verts, colors, cap);
+    else if (nb > 0)
+      k_mesh<RF_STORAGE_FP32><<<nb, 256, 0, st>>>(vol->dv, vol->dp.voxel, vol->dp.tau, pass, d_cnt, verts, colors, cap);
     s = check_cuda(vol, cudaGetLastError(), "mesh launch");
     if (s != RF_OK) return s;
     s = check_cuda(vol, cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st), "mesh count");

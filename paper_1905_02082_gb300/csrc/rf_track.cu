@@ -24,6 +24,7 @@
 // falls below the thresholds.  Results are deterministic: fixed grid, fixed
 // pixel-to-thread mapping, fixed reduction order.
 #include <cmath>
+#include <type_traits>
 
 #include "rf_volume.hpp"
 
@@ -35,6 +36,7 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return a * (
 // Trilinear SDF/intensity lookup with analytic gradients (per metre).
 // Corner n = dx + 2 dy + 4 dz.  Returns false unless all 8 corners exist and
 // were observed; *colour is true when all 8 also carry colour.
+template <int ST>
 __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p, float px, float py, float pz,
                                              float* V, float gV[3], float* I, float gI[3], bool* colour) {
   const float qx = px * p.inv_voxel, qy = py * p.inv_voxel, qz = pz * p.inv_voxel;
@@ -44,11 +46,15 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
   const float fx = qx - fkx, fy = qy - fky, fz = qz - fkz;
   const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
   const int bx = kx >> 3, by = ky >> 3, bz = kz >> 3;
-  uint2 c[8];
+  // FP32 storage: the uint2 words; FP16 storage: the 4-byte tracking words
+  using Word = typename std::conditional<ST == RF_STORAGE_FP32, uint2, unsigned>::type;
+  Word c[8];
   const int pool = hash_find(v, bx, by, bz);
   if (pool < 0) return false;
+  const Word* words = reinterpret_cast<const Word*>(v.vox);
+  const size_t stride = ST == RF_STORAGE_FP32 ? kBV : 2 * kBV;  // words per block
   if (lx < 7 && ly < 7 && lz < 7) {
-    const uint2* base = v.vox + (size_t)pool * kBV + lx + 8 * ly + 64 * lz;
+    const Word* base = words + (size_t)pool * stride + lx + 8 * ly + 64 * lz;
     c[0] = __ldg(base);
     c[1] = __ldg(base + 1);
     c[2] = __ldg(base + 8);
@@ -67,40 +73,59 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
       const int slot = (ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3);
       const int pn = nb[slot];
       if (pn < 0) return false;
-      c[n] = __ldg(v.vox + (size_t)pn * kBV + (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
+      c[n] = __ldg(words + (size_t)pn * stride + (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
     }
   }
   float F[8];
+  if constexpr (ST == RF_STORAGE_FP32) {
 #pragma unroll
-  for (int n = 0; n < 8; ++n) F[n] = __uint_as_float(c[n].x);
+    for (int n = 0; n < 8; ++n) F[n] = __uint_as_float(c[n].x);
+  } else {
+#pragma unroll
+    for (int n = 0; n < 8; ++n) F[n] = __half2float(__ushort_as_half((unsigned short)(c[n] & 0xFFFFu)));
+  }
+  // FP16 storage holds F / tau: values and gradients are scaled by tau once
+  const float sdf_scale = ST == RF_STORAGE_FP32 ? 1.0f : p.tau;
   const float c00 = lerpf(F[0], F[1], fx), c10 = lerpf(F[2], F[3], fx);
   const float c01 = lerpf(F[4], F[5], fx), c11 = lerpf(F[6], F[7], fx);
   const float c0 = lerpf(c00, c10, fy), c1 = lerpf(c01, c11, fy);
-  *V = lerpf(c0, c1, fz);
+  *V = lerpf(c0, c1, fz) * sdf_scale;
   // a never-observed corner stores NaN; every corner enters V with its
   // weight (0 * NaN = NaN), so one test covers all eight
   if (*V != *V) return false;
-  gV[0] = lerpf(lerpf(F[1] - F[0], F[3] - F[2], fy), lerpf(F[5] - F[4], F[7] - F[6], fy), fz) * p.inv_voxel;
-  gV[1] = lerpf(lerpf(F[2] - F[0], F[3] - F[1], fx), lerpf(F[6] - F[4], F[7] - F[5], fx), fz) * p.inv_voxel;
-  gV[2] = (c1 - c0) * p.inv_voxel;
-  // colour weights in the top bytes: their minimum over the corners
-  unsigned wmin = __vminu4(__vminu4(__vminu4(c[0].y, c[1].y), __vminu4(c[2].y, c[3].y)),
-                           __vminu4(__vminu4(c[4].y, c[5].y), __vminu4(c[6].y, c[7].y)));
-  const bool col = (wmin >> 24) != 0u;
-  *colour = col;
-  if (col) {
-    float In[8];  // intensities x 255e4, scaled once below
+  const float gs_v = p.inv_voxel * sdf_scale;
+  gV[0] = lerpf(lerpf(F[1] - F[0], F[3] - F[2], fy), lerpf(F[5] - F[4], F[7] - F[6], fy), fz) * gs_v;
+  gV[1] = lerpf(lerpf(F[2] - F[0], F[3] - F[1], fx), lerpf(F[6] - F[4], F[7] - F[5], fx), fz) * gs_v;
+  gV[2] = (c1 - c0) * gs_v;
+  float In[8];
+  float iscale;
+  if constexpr (ST == RF_STORAGE_FP32) {
+    // colour weights in the top bytes: their minimum over the corners
+    const unsigned wmin = __vminu4(__vminu4(__vminu4(c[0].y, c[1].y), __vminu4(c[2].y, c[3].y)),
+                                   __vminu4(__vminu4(c[4].y, c[5].y), __vminu4(c[6].y, c[7].y)));
+    *colour = (wmin >> 24) != 0u;
+    if (!*colour) return true;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) In[n] = rgb_intensity_raw(c[n].y);
-    const float d00 = lerpf(In[0], In[1], fx), d10 = lerpf(In[2], In[3], fx);
-    const float d01 = lerpf(In[4], In[5], fx), d11 = lerpf(In[6], In[7], fx);
-    const float d0 = lerpf(d00, d10, fy), d1 = lerpf(d01, d11, fy);
-    const float gs = kIntensityScale * p.inv_voxel;
-    *I = lerpf(d0, d1, fz) * kIntensityScale;
-    gI[0] = lerpf(lerpf(In[1] - In[0], In[3] - In[2], fy), lerpf(In[5] - In[4], In[7] - In[6], fy), fz) * gs;
-    gI[1] = lerpf(lerpf(In[2] - In[0], In[3] - In[1], fx), lerpf(In[6] - In[4], In[7] - In[5], fx), fz) * gs;
-    gI[2] = (d1 - d0) * gs;
+    for (int n = 0; n < 8; ++n) In[n] = rgb_intensity_raw(c[n].y);  // intensities x 255e4
+    iscale = kIntensityScale;
+  } else {
+    // I8 = 255 marks a corner without colour: the byte maximum over the corners
+    const unsigned imax = __vmaxu4(__vmaxu4(__vmaxu4(c[0], c[1]), __vmaxu4(c[2], c[3])),
+                                   __vmaxu4(__vmaxu4(c[4], c[5]), __vmaxu4(c[6], c[7])));
+    *colour = ((imax >> 16) & 255u) != 255u;
+    if (!*colour) return true;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) In[n] = (float)((c[n] >> 16) & 255u);  // intensities x 254
+    iscale = kI8Scale;
   }
+  const float d00 = lerpf(In[0], In[1], fx), d10 = lerpf(In[2], In[3], fx);
+  const float d01 = lerpf(In[4], In[5], fx), d11 = lerpf(In[6], In[7], fx);
+  const float d0 = lerpf(d00, d10, fy), d1 = lerpf(d01, d11, fy);
+  const float gs = iscale * p.inv_voxel;
+  *I = lerpf(d0, d1, fz) * iscale;
+  gI[0] = lerpf(lerpf(In[1] - In[0], In[3] - In[2], fy), lerpf(In[5] - In[4], In[7] - In[6], fy), fz) * gs;
+  gI[1] = lerpf(lerpf(In[2] - In[0], In[3] - In[1], fx), lerpf(In[6] - In[4], In[7] - In[5], fx), fz) * gs;
+  gI[2] = (d1 - d0) * gs;
   return true;
 }
 
@@ -370,6 +395,7 @@ __device__ __forceinline__ int chunk_pixels(int npix) { return npix >= (1 << 18)
 // One whole registration (see the file comment) run by a group of G CTAs,
 // this CTA being number lb of the group.  d.partials: 2 x 29 x max chunks
 // floats (double-buffered by evaluation parity); d.bar: a zeroed counter.
+template <int ST>
 __device__ void register_body(const RegDesc& d, int lb, int G) {
   __shared__ LMShared S;
   __shared__ float red[kRegWarps][29];
@@ -437,7 +463,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
           const float pz = R6 * x + R7 * y + R8 * D + t2;
           float V, gV[3], I, gI[3];
           bool colour;
-          if (!model_sample(d.v, p, px, py, pz, &V, gV, &I, gI, &colour)) continue;
+          if (!model_sample<ST>(d.v, p, px, py, pz, &V, gV, &I, gI, &colour)) continue;
           const float Jd[6] = {gV[0], gV[1], gV[2], py * gV[2] - pz * gV[1], pz * gV[0] - px * gV[2],
                                px * gV[1] - py * gV[0]};
           add_jtj(acc, Jd, V, 1.0f);
@@ -509,13 +535,15 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
 }
 
 // One registration on the whole grid.
-__global__ void __launch_bounds__(kRegThreads, 1) k_register(RegDesc d) { register_body(d, blockIdx.x, gridDim.x); }
+template <int ST>
+__global__ void __launch_bounds__(kRegThreads, 1) k_register(RegDesc d) { register_body<ST>(d, blockIdx.x, gridDim.x); }
 
 // Several independent registrations in one cooperative launch: CTA b runs
 // stream cta_stream[b] as member b - first[s] of a group of first[s+1] -
 // first[s] CTAs.  Groups never wait on each other.  A CTA mapped to stream
 // -1 has no work (streams that sit a batch out, or are on their first frame,
 // get no CTAs; the map is rewritten per batch without re-capturing the graph).
+template <int ST>
 __global__ void __launch_bounds__(kRegThreads, 1)
     k_register_batch(const RegDesc* __restrict__ descs, const int* __restrict__ cta_stream,
                      const int* __restrict__ first) {
@@ -524,14 +552,21 @@ __global__ void __launch_bounds__(kRegThreads, 1)
   if (s < 0) return;
   if (threadIdx.x == 0) sd = descs[s];
   __syncthreads();
-  register_body(sd, blockIdx.x - first[s], first[s + 1] - first[s]);
+  register_body<ST>(sd, blockIdx.x - first[s], first[s + 1] - first[s]);
 }
 
 }  // namespace
 
 int register_max_grid(int device) {
-  int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_register, kRegThreads, 0);
+  // the smallest residency over the kernels launched with this grid
+  const void* fns[] = {(const void*)k_register<RF_STORAGE_FP32>, (const void*)k_register<RF_STORAGE_FP16>,
+                       (const void*)k_register_batch<RF_STORAGE_FP32>, (const void*)k_register_batch<RF_STORAGE_FP16>};
+  int per_sm = 1 << 20, sms = 0;
+  for (const void* fn : fns) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kRegThreads, 0);
+    per_sm = n < per_sm ? n : per_sm;
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   return per_sm * sms;
 }
@@ -580,13 +615,17 @@ rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, 
   rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_regbar, 0, 2 * sizeof(unsigned), st), "barrier reset");
   if (s != RF_OK) return s;
   void* args[] = {&d};
-  return launch_coop(vol, (const void*)k_register, vol->reg_grid, args, st);
+  const void* fn = vol->p.storage == RF_STORAGE_FP16 ? (const void*)k_register<RF_STORAGE_FP16>
+                                                     : (const void*)k_register<RF_STORAGE_FP32>;
+  return launch_coop(vol, fn, vol->reg_grid, args, st);
 }
 
 rf_status launch_register_batch(rf_volume* vol, const RegDesc* descs, const int* cta_stream, const int* first,
                                 int total_ctas, cudaStream_t st) {
   void* args[] = {(void*)&descs, (void*)&cta_stream, (void*)&first};
-  return launch_coop(vol, (const void*)k_register_batch, total_ctas, args, st);
+  const void* fn = vol->p.storage == RF_STORAGE_FP16 ? (const void*)k_register_batch<RF_STORAGE_FP16>
+                                                     : (const void*)k_register_batch<RF_STORAGE_FP32>;
+  return launch_coop(vol, fn, total_ctas, args, st);
 }
 
 }  // namespace rf

@@ -22,6 +22,9 @@ STATUS_NAMES = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_CUDA", 3: "RF_ER
                 8: "RF_ERR_CAPACITY"}
 
 
+STORAGE_FP32, STORAGE_FP16 = 0, 1
+
+
 class RFError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -35,6 +38,7 @@ class rf_params(C.Structure):
         ("z_near", C.c_double), ("w_max", C.c_int), ("lm_iters", C.c_int * 3), ("lm_strides", C.c_int * 3),
         ("lm_lambda0", C.c_double), ("lm_eps_trans", C.c_double), ("lm_eps_rot", C.c_double),
         ("lm_min_valid", C.c_int), ("max_ff_sweeps", C.c_int), ("max_candidates", C.c_int64),
+        ("storage", C.c_int),
     ]
 
 

@@ -62,12 +62,13 @@ class StreamSpec:
     trunc: float = 0.1
     n_buckets: int = 1 << 18
     max_blocks: int = 100_000
+    storage: int = R.STORAGE_FP32
 
     def key(self):
-        return (self.width, self.height, self.voxel_size, self.trunc, self.n_buckets, self.max_blocks)
+        return (self.width, self.height, self.voxel_size, self.trunc, self.n_buckets, self.max_blocks, self.storage)
 
     def params(self):
-        return R.params(voxel_size=self.voxel_size, trunc=self.trunc)
+        return R.params(voxel_size=self.voxel_size, trunc=self.trunc, storage=self.storage)
 
     def footprint(self) -> int:
         return R.rf_volume_footprint(self.params(), self.n_buckets, self.max_blocks, self.width, self.height)
