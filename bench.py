@@ -5,7 +5,9 @@ One step = one whole frame through the public C ABI (rf_process_frame):
 registration -> residual mask -> registration without masked pixels ->
 integration with free-space carving, on the 640x480 static room workload
 (fx=fy=525, 1 cm voxels, tau 0.1 m, 2^20 hash buckets, seeded synthetic
-frames with Kinect-like noise).  Prints one JSON line.
+frames with Kinect-like noise).  Prints one JSON line.  The default run is
+the configuration's 300-frame forward trajectory (10 warm-up + 290 timed
+frames); runs asked for more frames than that play the 300 back and forth.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -46,6 +48,19 @@ def _render(args):
     seq = make_sequence(CONFIG, seed, n_frames=n)
     d, rgb, T, _ = seq.frame(i)
     return d, rgb, T
+
+
+MAX_RENDERED = 300  # the static configuration's length; longer runs play it back and forth
+
+
+def frame_order(n_rendered: int, n: int):
+    """Index of the rendered frame used at step n (0-based over warm-up and
+    timed steps): 0, 1, .., n_rendered-1, n_rendered-2, .., 1, 0, 1, .. so the
+    camera moves back and forth along the rendered trajectory."""
+    if n_rendered == 1:
+        return [0] * n
+    period = 2 * (n_rendered - 1)
+    return [k % period if k % period < n_rendered else period - k % period for k in range(n)]
 
 
 def make_frames(seed: int, n: int, workers: int):
@@ -162,7 +177,7 @@ class ClockSampler:
         self.gpu = gpu_index
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -298,13 +313,15 @@ def run_single(R, frames, K, cam, dev, stream, flush, args, storage):
                    voxel_size=VOXEL, trunc=TAU, storage=storage)
     T = torch.as_tensor(frames[0][2], device=dev).contiguous()
     Tn = torch.empty_like(T)
-    for i in range(args.warmup):
+    order = frame_order(len(frames), args.warmup + args.steps)
+    for w in range(args.warmup):
+        i = order[w]
         R.rf_process_frame(vol.h, vol.frame(d_depth[i], d_rgb[i], K), T, Tn, None, None, stream)
         T, Tn = Tn, T
     vol.sync()
     ms = []
     for k in range(args.steps):
-        i = args.warmup + k
+        i = order[args.warmup + k]
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -368,11 +385,11 @@ def run_batch(R, frames, K, cam, dev, stream, flush, args, storage=0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=290)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--batch-streams", type=int, default=32)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--serving-streams", type=int, default=32)
@@ -389,7 +406,8 @@ def main():
             run_reference(args)
         return
 
-    n_frames = args.warmup + args.steps
+    n_frames = min(args.warmup + args.steps, MAX_RENDERED)
+    order = frame_order(n_frames, args.warmup + args.steps)
     workers = min(16, os.cpu_count() or 1)
     frames = make_frames(seed=rank_seed(rank), n=n_frames, workers=workers)
     splan = serving_plan(args.serving_streams) if args.serving_streams > 0 and rank == 0 else []
@@ -423,14 +441,15 @@ def main():
     T = T0.clone()
     Tn = torch.empty_like(T)
     mask = torch.empty(cam.height, cam.width, dtype=torch.uint8, device=dev)
-    for i in range(args.warmup):
+    for w in range(args.warmup):
+        i = order[w]
         fr = vol.frame(d_depth[i], d_rgb[i], K)
         R.rf_process_frame(vol.h, fr, T, Tn, mask, None, stream)
         T, Tn = Tn, T
     vol.sync()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    profs, infos = [], []
+    profs, infos, errs = [], [], []
     info_dev = torch.zeros(ctypes.sizeof(R.rf_track_info), dtype=torch.uint8, device=dev)
     if dist:
         dist.barrier()
@@ -438,7 +457,7 @@ def main():
     clocks = ClockSampler(local)
     wall0 = time.perf_counter()
     for k in range(args.steps):
-        i = args.warmup + k
+        i = order[args.warmup + k]
         flush.zero_()  # L2 flush between steps, outside the step's events
         fr = vol.frame(d_depth[i], d_rgb[i], K)
         ev[k][0].record(stream)
@@ -447,6 +466,7 @@ def main():
         T, Tn = Tn, T
         profs.append(vol.profile(stream))  # synchronises; reads this frame's events
         infos.append(R.Volume.info_of(info_dev))
+        errs.append(float(np.linalg.norm(T.cpu().numpy()[:3, 3] - frames[i][2][:3, 3])))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -489,14 +509,15 @@ def main():
         h_rgb = [torch.from_numpy(f[1]).pin_memory() for f in frames]
         Th = np.ascontiguousarray(frames[0][2])
         To = np.zeros((4, 4))
-        for i in range(args.warmup):
+        for w in range(args.warmup):
+            i = order[w]
             R.rf_process_frame_host(vol2.h, h_depth[i].numpy(), h_rgb[i].numpy(), [K.fx, K.fy, K.cx, K.cy], Th, To,
                                     None, stream)
             Th = To.copy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(n_e2e):
-            i = args.warmup + k
+            i = order[args.warmup + k]
             R.rf_process_frame_host(vol2.h, h_depth[i].numpy(), h_rgb[i].numpy(), [K.fx, K.fy, K.cx, K.cy], Th, To,
                                     None, stream)
             Th = To.copy()
@@ -544,6 +565,8 @@ def main():
                                    "bytes_per_launch": statistics.mean(bytes_per),
                                    "launch_ms": statistics.mean(kern_ms)},
             "frame_hbm": {"achieved": frame_gbs, "peak": peak, "unit": "GB/s", "frac": frame_gbs / peak},
+            "tracking": {"rmse_m": float(np.sqrt(np.mean(np.square(errs)))), "max_m": float(np.max(errs)),
+                         "note": "free-running pose vs the ground truth of the timed frames (no loop closure)"},
             "work": {"updated_voxels": statistics.mean(upd), "new_blocks": statistics.mean(newb),
                      "candidates": statistics.mean(p.candidates for p in profs), "blocks": st.n_blocks,
                      "guard_pixels": statistics.mean(p.guard_pixels for p in profs)},

@@ -478,13 +478,24 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
             add_jtj(acc, Jc, rc, p.w_c);
           }
         }
-        // chunk partial: warp shuffles, then the warps in fixed order
+        // chunk partial: a butterfly over the warp that halves the vector at
+        // every step (31 shuffles for 32 slots) and leaves component c on
+        // lane c, then the warps in fixed order
+        {
+          float v[32];
 #pragma unroll
-        for (int i = 0; i < 29; ++i) {
-          float sv = acc[i];
+          for (int i = 0; i < 32; ++i) v[i] = i < 29 ? acc[i] : 0.0f;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-          if (lane == 0) red[warp][i] = sv;
+          for (int h = 16; h > 0; h >>= 1) {
+            const bool upper = (lane & h) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+              const float keep = upper ? v[i + h] : v[i];
+              const float send = upper ? v[i] : v[i + h];
+              v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+          }
+          if (lane < 29) red[warp][lane] = v[0];
         }
         __syncthreads();
         if (threadIdx.x < 29) {

@@ -437,8 +437,11 @@ def _rand_color(rng):
 
 
 def _rand_tex(rng):
-    return tuple(np.concatenate([rng.uniform(2.0, 9.0, size=3), rng.uniform(0, 2 * math.pi, size=3),
-                                 rng.uniform(3.0, 12.0, size=1), rng.uniform(0, 2 * math.pi, size=1)]))
+    """Albedo pattern frequencies (rad/m) and phases: wavelengths of about
+    9-40 cm, the scale of texture on indoor surfaces (a smoother albedo leaves
+    the colour term of the registration almost nothing to hold on to)."""
+    return tuple(np.concatenate([rng.uniform(16.0, 72.0, size=3), rng.uniform(0, 2 * math.pi, size=3),
+                                 rng.uniform(24.0, 96.0, size=1), rng.uniform(0, 2 * math.pi, size=1)]))
 
 
 def _ring_point(rng, rmin=1.0, rmax=1.7):
