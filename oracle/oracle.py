@@ -83,6 +83,8 @@ def _load():
         lib.orc_floodfill.argtypes = [u8p, C.c_void_p, C.c_int, C.c_int, C.c_int64, u8p]
         lib.orc_compute_mask.argtypes = [vp, C.POINTER(Frame), dp, u8p]
         lib.orc_process_frame.argtypes = [vp, C.POINTER(Frame), dp, dp, u8p, C.POINTER(TrackInfo)]
+        lib.orc_virtual_depth.argtypes = [vp, C.POINTER(Frame), dp, C.c_uint16, C.c_int, C.c_int,
+                                          C.POINTER(C.c_uint16)]
         lib.orc_se3_exp.argtypes = [dp, dp]
         lib.orc_lm_solve.restype = C.c_int
         lib.orc_lm_solve.argtypes = [dp, dp, C.c_double, dp]
@@ -221,6 +223,21 @@ class OracleVolume:
         m = np.zeros(f.shape, dtype=np.uint8)
         self.lib.orc_compute_mask(self.h, C.byref(f.c), _dptr(T), _vptr(m))
         return m
+
+    def virtual_depth(self, f: FrameData, T, far_raw: Optional[int] = None, rows=None):
+        """Sec. III-E, second option: f's depth with its zero pixels filled by
+        casting rays through this (temporary) model from pose T.  far_raw
+        defaults to d_max in raw units.  rows = (r0, r1) limits the work to
+        those rows (others are returned as 0)."""
+        T = _T(T)
+        if far_raw is None:
+            far_raw = int(round(self.params.d_max * self.params.depth_scale))
+        H, W = f.shape
+        r0, r1 = rows if rows is not None else (0, H)
+        out = np.zeros((H, W), dtype=np.uint16)
+        self.lib.orc_virtual_depth(self.h, C.byref(f.c), _dptr(T), far_raw, r0, r1,
+                                   out.ctypes.data_as(C.POINTER(C.c_uint16)))
+        return out
 
     def process_frame(self, f: FrameData, T_init):
         T = _T(T_init)

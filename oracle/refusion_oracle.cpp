@@ -18,7 +18,9 @@
 //   Sec. III-D  free-space carving: every non-occluded frustum voxel outside
 //               the truncation band (up to a clipping plane) is averaged
 //               towards tau.
-//   Sec. III-E  invalid (zero) depth is ignored (first option).
+//   Sec. III-E  invalid (zero) depth is ignored (first option); the second
+//               option's virtual depth: zero pixels filled from a temporary
+//               model by casting each pixel's ray through its TSDF.
 //   Tab. I      default parameters.
 //
 // Readings where the paper is silent (shared definition with the CUDA path):
@@ -773,6 +775,52 @@ void pack_H(const double H21[21], double Hm[6][6]) {
 // ---------------------------------------------------------------------------
 // C entry points
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// virtual depth (Sec. III-E, second option)
+// ---------------------------------------------------------------------------
+// Readings: ray samples at z_k = z_near + k v/2 (z along the optical axis),
+// k = 0 .. floor(2 (d_max - z_near) / v), computed on micrometres; a sample
+// counts when all 8 trilinear corners are observed; the virtual depth is the
+// first crossing from V > 0 to V <= 0 between two consecutive counted samples,
+// z* = z_{k-1} + (v/2) V_{k-1} / (V_{k-1} - V_k), rounded to the nearest raw
+// unit (half up); zero pixels without a crossing get far_raw.
+void virtual_depth(Volume& V, const orc_frame* f, const double T[16], uint16_t far_raw, int row0, int row1,
+                   uint16_t* out) {
+  const double delta = V.p.voxel_size * 0.5;
+  const int64_t K = (2 * (V.dmax_um - llround(V.p.z_near * 1e6))) / V.v_um;
+  for (int v = row0; v < row1; ++v)
+    for (int u = 0; u < f->width; ++u) {
+      const int idx = v * f->width + u;
+      if (f->depth[idx] != 0) {
+        out[idx] = f->depth[idx];
+        continue;
+      }
+      uint16_t result = far_raw;
+      bool prev_valid = false;
+      double prev_V = 0.0, prev_z = 0.0;
+      for (int64_t k = 0; k <= K; ++k) {
+        const double z = V.p.z_near + (double)k * delta;
+        double p[3];
+        backproject_world(f, u, v, z, T, p);
+        int64_t k0[3];
+        double fr[3];
+        Corners c;
+        const bool valid = cell_of(V, p, k0, fr) && gather(V, k0, &c);
+        const double Vk = valid ? trilinear(c.F, fr) : 0.0;
+        if (prev_valid && valid && prev_V > 0.0 && Vk <= 0.0) {
+          const double t = prev_V / (prev_V - Vk);
+          const double zs = prev_z + delta * t;
+          result = (uint16_t)std::floor(zs * V.p.depth_scale + 0.5);
+          break;
+        }
+        prev_valid = valid;
+        prev_V = Vk;
+        prev_z = z;
+      }
+      out[idx] = result;
+    }
+}
+
 extern "C" {
 
 void* orc_create(const orc_params* p) {
@@ -845,6 +893,11 @@ void orc_process_frame(void* vol, const orc_frame* f, const double T_init[16], d
   }
   if (mask_out) std::memcpy(mask_out, mask.data(), HW);
   V.frames++;
+}
+
+void orc_virtual_depth(void* vol, const orc_frame* f, const double T[16], uint16_t far_raw, int row0, int row1,
+                       uint16_t* out) {
+  virtual_depth(*static_cast<Volume*>(vol), f, T, far_raw, row0, row1, out);
 }
 
 void orc_se3_exp(const double xi[6], double T[16]) { se3_exp(xi, T); }

@@ -82,6 +82,12 @@ void orc_dilate3(const uint8_t* in, int H, int W, uint8_t* out);
 void orc_floodfill(const uint8_t* MR, const uint16_t* depth, int H, int W, int64_t theta_ppm, uint8_t* MD);
 void orc_compute_mask(void* vol, const orc_frame* f, const double T[16], uint8_t* mask);
 
+/* Virtual depth (Sec. III-E, second option) of rows [row0, row1): zero pixels of f->depth take the first
+ * positive-to-non-positive TSDF crossing along their ray seen from T (samples z_near + k voxel/2 up to
+ * d_max, linear interpolation, rounded to raw units), far_raw where there is none; other pixels are copied. */
+void orc_virtual_depth(void* vol, const orc_frame* f, const double T[16], uint16_t far_raw, int row0, int row1,
+                       uint16_t* out);
+
 /* Whole frame: track -> mask -> re-track -> integrate (first frame: integrate at T_init). */
 void orc_process_frame(void* vol, const orc_frame* f, const double T_init[16], double T_out[16],
                        uint8_t* mask_out, orc_track_info* info);

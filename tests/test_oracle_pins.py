@@ -678,3 +678,89 @@ def test_mesh_of_sphere_is_close_and_outward(oracle_mod):
     big = np.linalg.norm(n, axis=1) > 1e-10   # zero-area triangles at exact-zero corners carry no normal
     assert big.sum() > 0.9 * len(tris)
     assert np.all(np.einsum("ij,ij->i", n[big], tris[big].mean(axis=1) - c) > 0)
+
+
+# ---------------------------------------------------------------------------
+# virtual depth (Sec. III-E, second option)
+# ---------------------------------------------------------------------------
+
+def test_virtual_depth_of_a_fronto_parallel_plane_is_exact(oracle_mod):
+    """The projective TSDF of a fronto-parallel plane is affine in the band, so
+    the linear interpolation of the crossing recovers the plane depth exactly:
+    from the integrating pose, from a pose 10 cm closer, and from a pose moved
+    sideways (interior pixels whose rays stay in the observed region)."""
+    O = oracle_mod
+    cam = CAM_TINY
+    vol = O.OracleVolume(voxel_size=0.02, trunc=0.1)
+    depth, rgb = fronto_plane_frame(cam, 1503, (200, 100, 50))
+    vol.integrate(_frame(O, depth, rgb, cam), np.eye(4))
+    zero = np.zeros_like(depth)
+    f0 = _frame(O, zero, rgb, cam)
+    m = 12
+    out = vol.virtual_depth(f0, np.eye(4))
+    assert np.all(out[m:-m, m:-m] == 1503)
+    T = np.eye(4)
+    T[2, 3] = 0.1
+    assert np.all(vol.virtual_depth(f0, T)[m:-m, m:-m] == 1403)
+    T = np.eye(4)
+    T[0, 3] = 0.05
+    assert np.all(vol.virtual_depth(f0, T)[m:-m, m:-m] == 1503)
+
+
+def test_virtual_depth_fill_rules(oracle_mod):
+    """Non-zero pixels are copied unchanged (even outside the valid range);
+    zero pixels without a crossing get the far value (d_max by default)."""
+    O = oracle_mod
+    cam = CAM_TINY
+    vol = O.OracleVolume(voxel_size=0.02, trunc=0.1)
+    rng = np.random.default_rng(4)
+    depth = np.where(rng.random((cam.height, cam.width)) < 0.5, 0, rng.integers(1, 9000, (cam.height, cam.width)))
+    depth = depth.astype(np.uint16)
+    rgb = np.zeros((cam.height, cam.width, 3), np.uint8)
+    f = _frame(O, depth, rgb, cam)
+    out = vol.virtual_depth(f, np.eye(4))  # empty model: no crossing anywhere
+    np.testing.assert_array_equal(out[depth > 0], depth[depth > 0])
+    assert np.all(out[depth == 0] == 5000)
+    assert np.all(vol.virtual_depth(f, np.eye(4), far_raw=65535)[depth == 0] == 65535)
+    # a plane model fills exactly the zero pixels
+    plane, prgb = fronto_plane_frame(cam, 2000)
+    vol.integrate(_frame(O, plane, prgb, cam), np.eye(4))
+    out = vol.virtual_depth(f, np.eye(4))
+    np.testing.assert_array_equal(out[depth > 0], depth[depth > 0])
+    inner = np.zeros_like(depth, dtype=bool)
+    inner[12:-12, 12:-12] = True
+    assert np.all(out[(depth == 0) & inner] == 2000)
+
+
+def test_virtual_depth_of_a_sphere_matches_the_ray_intersection(oracle_mod):
+    """Integrated from one view and cast from the same view, the crossing lies
+    on the analytic sphere where the surface faces the camera (cos > 0.9),
+    within the error of the projective TSDF: a stored value takes the depth of
+    the voxel's nearest pixel, up to half a pixel off its ray, i.e. up to
+    0.5 z/fx tan(theta) of depth slope, plus 0.5 mm of depth quantisation."""
+    O = oracle_mod
+    cam = CAM_TINY
+    T = look_at([1.2, 0.2, 0.9], SPHERE.params["center"])
+    d, rgb, _ = render_frame([SPHERE], cam, T)
+    vol = O.OracleVolume(voxel_size=0.02, trunc=0.1)
+    vol.integrate(_frame(O, d, rgb, cam), T)
+    out = vol.virtual_depth(_frame(O, np.zeros_like(d), rgb, cam), T)
+    # analytic depth along each pixel ray (camera z), and the facing angle
+    c = np.linalg.inv(T)[:3, :3] @ SPHERE.params["center"] + np.linalg.inv(T)[:3, 3]
+    r = SPHERE.params["radius"]
+    u, v = np.meshgrid(np.arange(cam.width), np.arange(cam.height))
+    dirs = np.stack([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, np.ones_like(u, dtype=float)], -1)
+    a = (dirs * dirs).sum(-1)
+    b = -2 * (dirs * c).sum(-1)
+    disc = b * b - 4 * a * (c @ c - r * r)
+    hit = disc > 0
+    z = np.where(hit, (-b - np.sqrt(np.where(hit, disc, 0))) / (2 * a), 0.0)
+    p = dirs * z[..., None]
+    n = (p - c) / r
+    facing = np.where(hit, -(n * dirs).sum(-1) / np.sqrt(a), 0.0)
+    sel = hit & (facing > 0.9) & (d > 0)
+    assert sel.sum() > 500
+    err = np.abs(out[sel].astype(np.float64) - z[sel] * 1000.0)
+    tan = np.sqrt(np.clip(1.0 - facing[sel] ** 2, 0.0, None)) / facing[sel]
+    bound = 0.5 + 1000.0 * 0.5 * z[sel] / cam.fx * tan + 0.5  # + rounding of the result
+    assert np.all(err <= bound), float((err - bound).max())
