@@ -208,6 +208,23 @@ rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* frame, const d
 rf_status rf_integrate_frame(rf_volume* vol, const rf_frame* frame, const double* T_dev, const uint8_t* mask_dev,
                              void* stream);
 
+/* Virtual depth (Sec. III-E, second option).  Call it on a temporary volume
+ * that holds the n consecutive frames around the target frame, integrated at
+ * their registered poses (the caller builds it with rf_volume_reset and
+ * rf_integrate_frame; the paper uses n = 10).  Every zero pixel of
+ * frame->depth gets the depth of the first crossing of the volume's TSDF from
+ * V > 0 to V <= 0 along the pixel's ray seen from *T_dev: ray samples at
+ * z_k = z_near + k voxel/2 (depth along the optical axis) up to d_max, a
+ * sample counting when all 8 trilinear corners are observed, the crossing
+ * interpolated linearly between the two bracketing samples and rounded to the
+ * nearest raw unit.  Zero pixels without a crossing get far_raw (0 selects
+ * round(d_max * depth_scale): the clipping plane, so that such rays carve free
+ * space up to it); non-zero pixels are copied.  depth_out: device uint16
+ * height*width; it may be frame->depth itself (in-place fill).  Decisions are
+ * exact: FP32 with an error bound, FP64 re-evaluation near it.  Asynchronous. */
+rf_status rf_virtual_depth(rf_volume* vol, const rf_frame* frame, const double* T_dev, int far_raw,
+                           uint16_t* depth_out, void* stream);
+
 /* The whole per-frame loop (Fig. 2 / Sec. III-C): track -> mask -> track
  * without masked pixels -> integrate with that pose and mask.  The first frame
  * of an empty volume (new, reset, or imported from an empty snapshot) is

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librefusion.so")
-SOURCES = ["rf_api.cu", "rf_integrate.cu", "rf_track.cu", "rf_mask.cu", "rf_mesh.cu"]
+SOURCES = ["rf_api.cu", "rf_integrate.cu", "rf_track.cu", "rf_mask.cu", "rf_mesh.cu", "rf_raycast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-fast-math",
          "--fmad=true", "-I", INCLUDE, "-I", CSRC]

@@ -719,6 +719,16 @@ rf_status rf_compute_mask(rf_volume* vol, const rf_frame* frame, const double* T
   return launch_mask(vol, make_dev_frame(frame), T_dev, mask_dev, (cudaStream_t)stream);
 }
 
+rf_status rf_virtual_depth(rf_volume* vol, const rf_frame* frame, const double* T_dev, int far_raw,
+                           uint16_t* depth_out, void* stream) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (!frame_ok(vol, frame)) return set_error(vol, RF_ERR_INVALID_ARG, "invalid frame");
+  if (!T_dev || !depth_out) return set_error(vol, RF_ERR_INVALID_ARG, "NULL pose or output");
+  if (far_raw < 0 || far_raw > 65535) return set_error(vol, RF_ERR_INVALID_ARG, "far_raw must be in 0..65535");
+  const unsigned far = far_raw > 0 ? (unsigned)far_raw : (unsigned)llround(vol->p.d_max * vol->p.depth_scale);
+  return launch_virtual_depth(vol, make_dev_frame(frame), T_dev, far, depth_out, (cudaStream_t)stream);
+}
+
 rf_status rf_integrate_frame(rf_volume* vol, const rf_frame* frame, const double* T_dev, const uint8_t* mask_dev,
                              void* stream) {
   if (!vol) return RF_ERR_INVALID_ARG;

@@ -221,6 +221,47 @@ __device__ __forceinline__ unsigned rgb_i8(unsigned c) {
   return (254u * s + 1275000u) / 2550000u;
 }
 
+// FP64 lerp in the oracle's operation order (no contraction).
+__device__ __forceinline__ double lerp_rn(double a, double b, double t) {
+  const double om = __dsub_rn(1.0, t);
+  return __dadd_rn(__dmul_rn(a, om), __dmul_rn(b, t));
+}
+
+// Fetches the 8 corner SDF values of the cell with lattice origin k; false if
+// any corner is missing or unobserved.  FP16 storage: the stored value F16 x
+// tau (one float multiply, exactly what rf_volume_export returns).
+template <int ST>
+__device__ __forceinline__ bool corners_of(const DevVol& v, const DevParams& p, int kx, int ky, int kz, float F[8]) {
+  const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
+  if (pool < 0) return false;
+  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
+  auto value = [&](int pl, int i) -> float {
+    if constexpr (ST == RF_STORAGE_FP32) return __uint_as_float(__ldg(&v.vox[(size_t)pl * kBV + i].x));
+    else return trk_sdf(__ldg(trk_words(v, pl) + i), p.tau);
+  };
+  if (lx < 7 && ly < 7 && lz < 7) {  // all 8 corners in one block
+    const int base = lx + 8 * ly + 64 * lz;
+    const int off[8] = {0, 1, 8, 9, 64, 65, 72, 73};
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      F[n] = value(pool, base + off[n]);
+      if (F[n] != F[n]) return false;
+    }
+    return true;
+  }
+  const int4 n0 = __ldg(v.nbr + 2 * (size_t)pool), n1 = __ldg(v.nbr + 2 * (size_t)pool + 1);
+  const int nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const int ix = lx + (n & 1), iy = ly + ((n >> 1) & 1), iz = lz + ((n >> 2) & 1);
+    const int pn = nb[(ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3)];
+    if (pn < 0) return false;
+    F[n] = value(pn, (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
+    if (F[n] != F[n]) return false;
+  }
+  return true;
+}
+
 __device__ __forceinline__ bool pixel_valid(const DevParams& p, unsigned raw) {
   if (p.du_um < 32768) {  // raw * du fits 31 bits
     const int D = (int)raw * (int)p.du_um;
@@ -309,6 +350,8 @@ rf_status check_cuda(rf_volume* vol, cudaError_t e, const char* what);
 rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
                        rf_track_info* info, cudaStream_t st);
 rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_t* mask_out, cudaStream_t st);
+rf_status launch_virtual_depth(rf_volume* vol, const DevFrame& f, const double* T, unsigned far_raw, uint16_t* out,
+                               cudaStream_t st);
 rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st);
 // profiling events (no-ops unless profiling is enabled); ids below
 enum ProfEvent { EV_FRAME0, EV_TRACK1_END, EV_MASK_END, EV_TRACK2_END, EV_INTEG0, EV_KERNEL0, EV_KERNEL1, EV_FRAME1,

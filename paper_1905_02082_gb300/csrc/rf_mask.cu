@@ -24,46 +24,6 @@
 namespace rf {
 namespace {
 
-__device__ __forceinline__ double lerp_rn(double a, double b, double t) {
-  const double om = __dsub_rn(1.0, t);
-  return __dadd_rn(__dmul_rn(a, om), __dmul_rn(b, t));
-}
-
-// Fetches the 8 corner SDF values of the cell with lattice origin k; false if
-// any corner is missing or unobserved.  FP16 storage: the stored value F16 x
-// tau (one float multiply, exactly what rf_volume_export returns).
-template <int ST>
-__device__ __forceinline__ bool corners_of(const DevVol& v, const DevParams& p, int kx, int ky, int kz, float F[8]) {
-  const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
-  if (pool < 0) return false;
-  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
-  auto value = [&](int pl, int i) -> float {
-    if constexpr (ST == RF_STORAGE_FP32) return __uint_as_float(__ldg(&v.vox[(size_t)pl * kBV + i].x));
-    else return trk_sdf(__ldg(trk_words(v, pl) + i), p.tau);
-  };
-  if (lx < 7 && ly < 7 && lz < 7) {  // all 8 corners in one block
-    const int base = lx + 8 * ly + 64 * lz;
-    const int off[8] = {0, 1, 8, 9, 64, 65, 72, 73};
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-      F[n] = value(pool, base + off[n]);
-      if (F[n] != F[n]) return false;
-    }
-    return true;
-  }
-  const int4 n0 = __ldg(v.nbr + 2 * (size_t)pool), n1 = __ldg(v.nbr + 2 * (size_t)pool + 1);
-  const int nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-#pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    const int ix = lx + (n & 1), iy = ly + ((n >> 1) & 1), iz = lz + ((n >> 2) & 1);
-    const int pn = nb[(ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3)];
-    if (pn < 0) return false;
-    F[n] = value(pn, (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
-    if (F[n] != F[n]) return false;
-  }
-  return true;
-}
-
 // FP64 residual in the fixed evaluation order; r < 0 when the lookup is invalid.
 template <int ST>
 __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevParams& p, const double* T, int u, int vv,

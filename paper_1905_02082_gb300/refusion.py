@@ -75,6 +75,7 @@ SIGNATURES = [
     ("rf_compute_mask", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
     ("rf_compute_mask_noalloc", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
     ("rf_integrate_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp]),
+    ("rf_virtual_depth", _int, [_vp, C.POINTER(rf_frame), _vp, _int, _vp, _vp]),
     ("rf_process_frame", _int, [_vp, C.POINTER(rf_frame), _vp, _vp, _vp, _vp, _vp]),
     ("rf_process_frame_host", _int, [_vp, _int, _int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("rf_extract_mesh", _int, [_vp, _vp, _vp, _i64, C.POINTER(_i64), _vp]),
@@ -201,6 +202,10 @@ def rf_integrate_frame(h, frame: rf_frame, T, mask=None, stream=None):
     _check(load().rf_integrate_frame(h, C.byref(frame), _ptr(T), _ptr(mask), _stream(stream)), h)
 
 
+def rf_virtual_depth(h, frame: rf_frame, T, far_raw, depth_out, stream=None):
+    _check(load().rf_virtual_depth(h, C.byref(frame), _ptr(T), int(far_raw), _ptr(depth_out), _stream(stream)), h)
+
+
 def rf_process_frame(h, frame: rf_frame, T_init, T_out, mask_out=None, info=None, stream=None):
     _check(load().rf_process_frame(h, C.byref(frame), _ptr(T_init), _ptr(T_out), _ptr(mask_out), _ptr(info),
                                    _stream(stream)), h)
@@ -296,6 +301,15 @@ class Volume:
 
     def integrate(self, frame: rf_frame, T, mask=None, stream=None):
         rf_integrate_frame(self.h, frame, self._pose(T), mask, stream)
+
+    def virtual_depth(self, frame: rf_frame, T, far_raw: int = 0, out=None, stream=None):
+        """Depth of `frame` with its zero pixels filled from this volume (used
+        as the temporary model of Sec. III-E's second option)."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty(frame.height, frame.width, dtype=torch.uint16, device=self.dev)
+        rf_virtual_depth(self.h, frame, self._pose(T), far_raw, out, stream)
+        return out
 
     def process(self, frame: rf_frame, T_init, mask_out=None, stream=None):
         torch = self.torch
