@@ -336,6 +336,54 @@ def run_single(R, frames, K, cam, dev, stream, flush, args, storage):
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}}
 
 
+def run_virtual_depth(R, frames, K, cam, dev, stream, args, n_window=10):
+    """Sec. III-E, second option, on the static workload: for each target
+    frame, the temporary model of the n_window frames starting at it
+    (integrated at their poses, here the ground truth) and the fill of the
+    target's zero pixels (its edge dropout).  Per filled frame: the whole
+    cost (reset + n_window integrations + ray casting, host clock around a
+    synchronised sequence) and the ray-casting kernel alone (CUDA events)."""
+    import torch
+    n_targets = min(args.vd_frames, len(frames) - n_window)
+    if n_targets <= 0:
+        return None
+    tmp = R.Volume(n_buckets=1 << 18, max_blocks=100_000, max_width=cam.width, max_height=cam.height,
+                   voxel_size=VOXEL, trunc=TAU)
+    d_depth = [torch.from_numpy(f[0].astype(np.int32)).to(dev).to(torch.uint16).contiguous() for f in frames]
+    d_rgb = [torch.from_numpy(f[1]).to(dev).contiguous() for f in frames]
+    Ts = [torch.as_tensor(f[2], device=dev).contiguous() for f in frames]
+    out = torch.empty(cam.height, cam.width, dtype=torch.uint16, device=dev)
+    far = int(round(tmp.params.d_max * tmp.params.depth_scale))
+    total_ms, cast_ms, holes, filled = [], [], [], []
+    for t in range(-2, n_targets):  # two untimed warm-up targets
+        i = max(t, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tmp.reset()
+        for j in range(i, i + n_window):
+            R.rf_integrate_frame(tmp.h, tmp.frame(d_depth[j], d_rgb[j], K), Ts[j], None, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        R.rf_virtual_depth(tmp.h, tmp.frame(d_depth[i], d_rgb[i], K), Ts[i], 0, out, stream)
+        b.record(stream)
+        b.synchronize()
+        t1 = time.perf_counter()
+        tmp.sync(stream)
+        if t < 0:
+            continue
+        total_ms.append(1000.0 * (t1 - t0))
+        cast_ms.append(a.elapsed_time(b))
+        zero = d_depth[i] == 0
+        holes.append(int(zero.sum().item()))
+        filled.append(int((zero & (out != far)).sum().item()))
+    tmp.close()
+    return {"window": n_window, "targets": n_targets, "ms_per_filled_frame": statistics.mean(total_ms),
+            "raycast_ms": statistics.mean(cast_ms), "holes_per_frame": statistics.mean(holes),
+            "filled_fraction": sum(filled) / max(1, sum(holes)),
+            "note": "temporary model of the 10 frames starting at the target (ground-truth poses), rebuilt per "
+                    "target; holes = the frames' zero pixels (5 % edge dropout)"}
+
+
 def run_batch(R, frames, K, cam, dev, stream, flush, args, storage=0):
     """S streams (one volume each, the same rendered sequence) processed in
     lockstep batches through rf_batch_process: aggregate frames/s and the
@@ -392,6 +440,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--batch-streams", type=int, default=32)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--vd-frames", type=int, default=20)
     ap.add_argument("--serving-streams", type=int, default=32)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-clip", type=int, default=3)
@@ -538,6 +587,7 @@ def main():
         batch = run_batch(R, frames, K, cam, dev, stream, flush, args)
         batch_fp16 = run_batch(R, frames, K, cam, dev, stream, flush, args, storage=R.STORAGE_FP16)
     single_fp16 = run_single(R, frames, K, cam, dev, stream, flush, args, storage=R.STORAGE_FP16)
+    virtual_depth = run_virtual_depth(R, frames, K, cam, dev, stream, args) if args.vd_frames > 0 else None
     serving = run_serving(R, splan, clips, args) if splan else None
 
     if rank == 0:
@@ -573,6 +623,7 @@ def main():
             "batch": batch,
             "batch_fp16": batch_fp16,
             "single_fp16": single_fp16,
+            "virtual_depth": virtual_depth,
             "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
