@@ -953,6 +953,26 @@ rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coor
   return rf_sync_status(vol, nullptr);
 }
 
+rf_status rf_get_launch_config(rf_volume* vol, rf_launch_config* out) {
+  if (!vol || !out) return RF_ERR_INVALID_ARG;
+  *out = vol->launch;
+  return RF_OK;
+}
+
+rf_status rf_set_launch_config(rf_volume* vol, const rf_launch_config* cfg) {
+  if (!vol || !cfg) return RF_ERR_INVALID_ARG;
+  const int v[4] = {cfg->integrate_ctas_per_sm, cfg->cull_ctas_per_sm, cfg->fixup_ctas_per_sm,
+                    cfg->raycast_ctas_per_sm};
+  for (int x : v)
+    if (x < 1 || x > 64) return set_error(vol, RF_ERR_INVALID_ARG, "CTAs per SM must be in 1..64");
+  rf_status s = check_cuda(vol, cudaDeviceSynchronize(), "launch config sync");
+  if (s) return s;
+  for (auto& g : vol->graphs) cudaGraphExecDestroy(g.exec);  // they hold the old shapes
+  vol->graphs.clear();
+  vol->launch = *cfg;
+  return RF_OK;
+}
+
 rf_status rf_volume_stats(rf_volume* vol, rf_stats* out) {
   if (!vol || !out) return RF_ERR_INVALID_ARG;
   int nb = 0;

@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(256) k_nbr_fixup(DevVol v, const int* __restri
 }  // namespace
 
 rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st, const int* gate) {
-  k_nbr_fixup<<<vol->sm_count * 2, 256, 0, st>>>(vol->dv, lo_ptr, lo, gate);
+  k_nbr_fixup<<<vol->sm_count * vol->launch.fixup_ctas_per_sm, 256, 0, st>>>(vol->dv, lo_ptr, lo, gate);
   return check_cuda(vol, cudaGetLastError(), "neighbour table launch");
 }
 
@@ -572,14 +572,14 @@ rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, c
   k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks, f.gate);
   k_tilemax<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x);
   k_integ_aabb<<<1, 32, 0, st>>>(T, f, vol->dp, vol->d_integ);
-  k_cull<<<vol->sm_count * 8, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
+  k_cull<<<vol->sm_count * vol->launch.cull_ctas_per_sm, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
                                             vol->p.max_candidates, vol->d_status);
   prof_record(vol, EV_KERNEL0, st);
   if (vol->p.storage == RF_STORAGE_FP16)
-    k_integrate<RF_STORAGE_FP16><<<vol->sm_count * 16, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
+    k_integrate<RF_STORAGE_FP16><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
                                                                              vol->d_cand, vol->p.max_candidates);
   else
-    k_integrate<RF_STORAGE_FP32><<<vol->sm_count * 16, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
+    k_integrate<RF_STORAGE_FP32><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
                                                                              vol->d_cand, vol->p.max_candidates);
   prof_record(vol, EV_KERNEL1, st);
   rf_status s = check_cuda(vol, cudaGetLastError(), "integrate launch");

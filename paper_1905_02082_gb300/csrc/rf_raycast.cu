@@ -220,7 +220,7 @@ rf_status launch_virtual_depth(rf_volume* vol, const DevFrame& f, const double* 
   if (s == RF_OK) s = check_cuda(vol, cudaMemsetAsync(vol->d_guard, 0, sizeof(unsigned), st), "guard reset");
   if (s != RF_OK) return s;
   k_vd_holes<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(f, out, list, count);
-  const int grid = vol->sm_count * 8;
+  const int grid = vol->sm_count * vol->launch.raycast_ctas_per_sm;
   if (vol->p.storage == RF_STORAGE_FP16)
     k_vd_cast<RF_STORAGE_FP16><<<grid, 256, 0, st>>>(vol->dv, f, vol->dp, T, far_raw, K, znear_d, delta_d, list, count,
                                                      out, vol->d_guard);

@@ -63,6 +63,11 @@ class rf_profile(C.Structure):
                 ("updated_voxels", C.c_int64), ("new_blocks", C.c_int64), ("guard_pixels", C.c_int64)]
 
 
+class rf_launch_config(C.Structure):
+    _fields_ = [("integrate_ctas_per_sm", C.c_int), ("cull_ctas_per_sm", C.c_int), ("fixup_ctas_per_sm", C.c_int),
+                ("raycast_ctas_per_sm", C.c_int)]
+
+
 # (name, restype, argtypes) of every entry point of refusion.h
 _vp, _i64, _int = C.c_void_p, C.c_int64, C.c_int
 SIGNATURES = [
@@ -82,6 +87,8 @@ SIGNATURES = [
     ("rf_volume_export", _int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, C.POINTER(_i64)]),
     ("rf_volume_import", _int, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     ("rf_volume_stats", _int, [_vp, C.POINTER(rf_stats)]),
+    ("rf_get_launch_config", _int, [_vp, C.POINTER(rf_launch_config)]),
+    ("rf_set_launch_config", _int, [_vp, C.POINTER(rf_launch_config)]),
     ("rf_batch_create", _int, [_vp, _int, C.POINTER(_vp)]),
     ("rf_batch_destroy", _int, [_vp]),
     ("rf_batch_process", _int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -251,16 +258,48 @@ def params(**overrides) -> rf_params:
     return p
 
 
+TUNING_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning")
+
+
+def tuning_path(device=None) -> str:
+    """Launch-shape table of the autotuner for a device (name and SM count)."""
+    import torch
+    prop = torch.cuda.get_device_properties(device if device is not None else torch.cuda.current_device())
+    name = "".join(ch if ch.isalnum() else "_" for ch in prop.name)
+    return os.path.join(TUNING_DIR, f"{name}_{prop.multi_processor_count}sm.json")
+
+
+_tuned = {}
+
+
+def tuned_launch_config(device=None) -> Optional[rf_launch_config]:
+    """The autotuned launch shapes of this device, or None without a table."""
+    path = tuning_path(device)
+    if path not in _tuned:
+        cfg = None
+        if os.path.exists(path):
+            import json
+            d = json.load(open(path))["launch"]
+            cfg = rf_launch_config(**{k: int(d[k]) for k, _ in rf_launch_config._fields_})
+        _tuned[path] = cfg
+    return _tuned[path]
+
+
 class Volume:
-    """A device-resident voxel-hashed TSDF volume (one camera stream)."""
+    """A device-resident voxel-hashed TSDF volume (one camera stream).  The
+    autotuned launch shapes of the device are applied when a table exists
+    (tune=False keeps the library defaults)."""
 
     def __init__(self, p: Optional[rf_params] = None, n_buckets: int = 1 << 20, max_blocks: int = 1 << 18,
-                 max_width: int = 640, max_height: int = 480, **overrides):
+                 max_width: int = 640, max_height: int = 480, tune: bool = True, **overrides):
         import torch
         self.torch = torch
         self.params = p if p is not None else params(**overrides)
         self.h = rf_create_volume(self.params, n_buckets, max_blocks, max_width, max_height)
         self.dev = torch.device("cuda", torch.cuda.current_device())
+        cfg = tuned_launch_config() if tune else None
+        if cfg is not None:
+            self.set_launch_config(cfg)
 
     def close(self):
         if getattr(self, "h", None):
@@ -330,6 +369,14 @@ class Volume:
 
     def sync(self, stream=None):
         rf_sync_status(self.h, stream)
+
+    def launch_config(self) -> rf_launch_config:
+        out = rf_launch_config()
+        _check(load().rf_get_launch_config(self.h, C.byref(out)), self.h)
+        return out
+
+    def set_launch_config(self, cfg: rf_launch_config):
+        _check(load().rf_set_launch_config(self.h, C.byref(cfg)), self.h)
 
     def set_profiling(self, enable: bool):
         _check(load().rf_set_profiling(self.h, 1 if enable else 0), self.h)
