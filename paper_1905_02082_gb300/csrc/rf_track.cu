@@ -391,6 +391,7 @@ constexpr int kRegWarps = kRegThreads / 32;
 // (512, or 2048 from 2^18 pixels), so the partials, and thus the result, do
 // not depend on how many CTAs run the registration.
 __device__ __forceinline__ int chunk_pixels(int npix) { return npix >= (1 << 18) ? 4 * kRegThreads : kRegThreads; }
+constexpr int kMaxPerThread = 4;  // pixels of one chunk per thread (chunk_pixels / kRegThreads at most)
 
 // One whole registration (see the file comment) run by a group of G CTAs,
 // this CTA being number lb of the group.  d.partials: 2 x 29 x max chunks
@@ -447,15 +448,42 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
 #pragma unroll
         for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
         const int end = min(npix, (ch + 1) * chunk);
-        for (int i = ch * chunk + threadIdx.x; i < end; i += kRegThreads) {
-          int row = (int)(((unsigned long long)i * magic) >> 32);
-          if (row * Ws > i) --row;
-          else if ((row + 1) * Ws <= i) ++row;
-          const int u = (i - row * Ws) * stride, vv = row * stride;
-          const int idx = vv * f.W + u;
-          const unsigned raw = __ldg(f.depth + idx);
+        // this thread's pixels of the chunk (at most kMaxPerThread): depth,
+        // mask and colour loaded up front, so their latencies overlap; the
+        // samples are then taken in the same order as the pixels
+        unsigned praw[kMaxPerThread], puv[kMaxPerThread], prgb[kMaxPerThread];
+#pragma unroll
+        for (int j = 0; j < kMaxPerThread; ++j) {
+          const int i = ch * chunk + threadIdx.x + j * kRegThreads;
+          praw[j] = 0u;
+          puv[j] = 0u;
+          prgb[j] = 0u;
+          if (i < end) {
+            int row = (int)(((unsigned long long)i * magic) >> 32);
+            if (row * Ws > i) --row;
+            else if ((row + 1) * Ws <= i) ++row;
+            const int u = (i - row * Ws) * stride, vv = row * stride;
+            const int idx = vv * f.W + u;
+            unsigned raw = __ldg(f.depth + idx);
+            if (d.mask && __ldg(d.mask + idx)) raw = 0u;  // masked: not sampled
+            const uint8_t* cp = f.rgb + 3 * (size_t)idx;
+            praw[j] = raw;
+            puv[j] = (unsigned)u | ((unsigned)vv << 16);
+            prgb[j] = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
+          }
+        }
+#pragma unroll 1
+        for (int j = 0; j < kMaxPerThread; ++j) {
+          // the next pixel's values rotate into slot 0 (registers, no local memory)
+          const unsigned raw = praw[0], uvj = puv[0], rgbj = prgb[0];
+#pragma unroll
+          for (int r = 0; r + 1 < kMaxPerThread; ++r) {
+            praw[r] = praw[r + 1];
+            puv[r] = puv[r + 1];
+            prgb[r] = prgb[r + 1];
+          }
           if (!pixel_valid(p, raw)) continue;
-          if (d.mask && __ldg(d.mask + idx)) continue;
+          const int u = (int)(uvj & 0xFFFFu), vv = (int)(uvj >> 16);
           const float D = (float)raw * p.inv_depth_scale;
           const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
           const float px = R0 * x + R1 * y + R2 * D + t0;
@@ -469,10 +497,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
           add_jtj(acc, Jd, V, 1.0f);
           acc[28] += 1.0f;
           if (colour) {
-            const uint8_t* cp = f.rgb + 3 * (size_t)idx;
-            const unsigned cc =
-                (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
-            const float rc = I - rgb_intensity_raw(cc) * kIntensityScale;
+            const float rc = I - rgb_intensity_raw(rgbj) * kIntensityScale;
             const float Jc[6] = {gI[0], gI[1], gI[2], py * gI[2] - pz * gI[1], pz * gI[0] - px * gI[2],
                                  px * gI[1] - py * gI[0]};
             add_jtj(acc, Jc, rc, p.w_c);
