@@ -23,6 +23,8 @@ import numpy as np
 
 from . import refusion as R
 
+MIN_GAIN = 0.02  # required improvement over the default
+
 CANDIDATES = {
     "integrate_ctas_per_sm": (4, 8, 12, 16, 24, 32, 48),
     "cull_ctas_per_sm": (2, 4, 8, 16, 32),
@@ -91,7 +93,7 @@ def _raycast_ms(cfg, cam, dev_frames, poses, K, reps):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--frames", type=int, default=24)
-    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     import torch
@@ -104,15 +106,22 @@ def main(argv=None):
                    torch.from_numpy(np.ascontiguousarray(rgb)).to(dev)) for d, rgb, _, _ in frames]
     poses = [torch.as_tensor(T, device=dev).contiguous() for _, _, T, _ in frames]
     cfg = R.rf_launch_config(16, 8, 2, 8)
+    defaults = {k: getattr(cfg, k) for k, _ in R.rf_launch_config._fields_}
     measured = {}
     t0 = time.time()
     for name, cands in CANDIDATES.items():
         times = {}
+        setattr(cfg, name, defaults[name])
         for v in cands:
             setattr(cfg, name, v)
             f = _raycast_ms if name == "raycast_ctas_per_sm" else _integration_ms
             times[v] = f(cfg, cam, dev_frames, poses, K, args.reps)
+        # a candidate replaces the current value only when it is clearly faster
+        # (differences within the run-to-run noise keep the default)
+        current = defaults[name]
         best = min(times, key=times.get)
+        if times[best] > (1.0 - MIN_GAIN) * times[current]:
+            best = current
         setattr(cfg, name, best)
         measured[name] = {str(k): round(v, 5) for k, v in times.items()}
         print(f"{name}: {best}  ({', '.join(f'{k}: {v:.4f} ms' for k, v in times.items())})", flush=True)
@@ -122,7 +131,8 @@ def main(argv=None):
     table = {"device": prop.name, "sm_count": prop.multi_processor_count,
              "launch": {k: getattr(cfg, k) for k, _ in R.rf_launch_config._fields_},
              "objective": "median device time of the integration stage (static room 640x480, 1 cm) and of "
-                          "virtual-depth ray casting; coordinate descent from the library defaults",
+                          "virtual-depth ray casting; coordinate descent from the library defaults, a candidate "
+                          f"kept only when {100 * MIN_GAIN:.0f} % faster than the default",
              "measured_ms": measured, "seconds": round(time.time() - t0, 1)}
     with open(out, "w") as fh:
         json.dump(table, fh, indent=1)

@@ -152,7 +152,8 @@ rf_status volume_buffers(rf_volume* vol, const rf_params* p, int64_t n_buckets, 
       (s = A(&vol->d_integ, 1, "integ")) || (s = A(&vol->d_tilemax, ntiles, "tiles")) ||
       (s = A(&vol->d_cand, (size_t)p->max_candidates, "candidates")) || (s = A(&vol->d_depth, npix, "depth staging")) ||
       (s = A(&vol->d_rgb, npix * 3, "rgb staging")) || (s = A(&vol->d_mask, npix, "mask staging")) ||
-      (s = A(&vol->d_T, 48, "poses")) || (s = A(&vol->d_info, 1, "info")) || (s = A(&vol->d_guard, 1, "guard count")))
+      (s = A(&vol->d_T, 48, "poses")) || (s = A(&vol->d_info, 1, "info")) || (s = A(&vol->d_guard, 1, "guard count")) ||
+      (s = A(&vol->d_pxcache, npix, "pixel block cache")))
     return s;
   return RF_OK;
 }
@@ -223,6 +224,11 @@ rf_status clear_model(rf_volume* vol, cudaStream_t st) {
   if (s) return s;
   if ((s = check_cuda(vol, cudaMemsetAsync(vol->d_nblocks, 0, sizeof(int), st), "pool reset"))) return s;
   if ((s = check_cuda(vol, cudaMemsetAsync(vol->d_coords, 0, sizeof(int4) * vol->max_blocks, st), "coords reset")))
+    return s;
+  // pools are reassigned from now on: forget every pixel's cached block
+  if ((s = check_cuda(vol, cudaMemsetAsync(vol->d_pxcache, 0xFF,
+                                           sizeof(unsigned long long) * (size_t)vol->max_w * vol->max_h, st),
+                      "pixel cache reset")))
     return s;
   return RF_OK;
 }
@@ -607,7 +613,7 @@ rf_status rf_destroy_volume(rf_volume* vol) {
   void* dev[] = {vol->d_hash, vol->d_vox,  vol->d_W,       vol->d_coords, vol->d_nbr, vol->d_nblocks, vol->d_status,
                  vol->d_regbar, vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
                  vol->d_tilemax, vol->d_cand, vol->d_depth, vol->d_rgb,   vol->d_mask,    vol->d_T, vol->d_info,
-                 vol->d_guard};
+                 vol->d_guard, vol->d_pxcache};
   for (void* p : dev)
     if (p) cudaFree(p);
   delete vol;

@@ -117,6 +117,10 @@ struct RegDesc {
   int max_chunks;
   unsigned* bar;
   unsigned* status;
+  // per full-resolution pixel: the (block key << 22 | pool) its last sample
+  // was found in, ~0 when none; a block's pool never changes until the
+  // volume is reset or imported, which clear the cache
+  unsigned long long* pxcache;
 };
 
 // Quantised pose and the frustum search region of one integration.

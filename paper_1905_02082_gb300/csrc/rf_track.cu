@@ -36,9 +36,12 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return a * (
 // Trilinear SDF/intensity lookup with analytic gradients (per metre).
 // Corner n = dx + 2 dy + 4 dz.  Returns false unless all 8 corners exist and
 // were observed; *colour is true when all 8 also carry colour.
+// cached: the pixel's (key << 22 | pool) from an earlier sample, ~0 if none;
+// *fresh receives a new entry when the block had to be looked up.
 template <int ST>
 __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p, float px, float py, float pz,
-                                             float* V, float gV[3], float* I, float gI[3], bool* colour) {
+                                             float* V, float gV[3], float* I, float gI[3], bool* colour,
+                                             unsigned long long cached, unsigned long long* fresh) {
   const float qx = px * p.inv_voxel, qy = py * p.inv_voxel, qz = pz * p.inv_voxel;
   if (!(fabsf(qx) < 1.0e6f && fabsf(qy) < 1.0e6f && fabsf(qz) < 1.0e6f)) return false;
   const float fkx = floorf(qx), fky = floorf(qy), fkz = floorf(qz);
@@ -49,8 +52,16 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
   // FP32 storage: the uint2 words; FP16 storage: the 4-byte tracking words
   using Word = typename std::conditional<ST == RF_STORAGE_FP32, uint2, unsigned>::type;
   Word c[8];
-  const int pool = hash_find(v, bx, by, bz);
-  if (pool < 0) return false;
+  if (!coord_ok(bx, by, bz)) return false;
+  const unsigned long long key = pack_key(bx, by, bz);
+  int pool;
+  if (cached != kEmpty && (cached >> 22) == key) {
+    pool = (int)(cached & 0x3FFFFFull);  // same block as last time: no hash probe
+  } else {
+    pool = hash_find(v, bx, by, bz);
+    if (pool < 0) return false;
+    *fresh = (key << 22) | (unsigned long long)pool;
+  }
   const Word* words = reinterpret_cast<const Word*>(v.vox);
   const size_t stride = ST == RF_STORAGE_FP32 ? kBV : 2 * kBV;  // words per block
   if (lx < 7 && ly < 7 && lz < 7) {
@@ -452,12 +463,14 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
         // mask and colour loaded up front, so their latencies overlap; the
         // samples are then taken in the same order as the pixels
         unsigned praw[kMaxPerThread], puv[kMaxPerThread], prgb[kMaxPerThread];
+        unsigned long long pcache[kMaxPerThread];
 #pragma unroll
         for (int j = 0; j < kMaxPerThread; ++j) {
           const int i = ch * chunk + threadIdx.x + j * kRegThreads;
           praw[j] = 0u;
           puv[j] = 0u;
           prgb[j] = 0u;
+          pcache[j] = kEmpty;
           if (i < end) {
             int row = (int)(((unsigned long long)i * magic) >> 32);
             if (row * Ws > i) --row;
@@ -469,6 +482,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
             const uint8_t* cp = f.rgb + 3 * (size_t)idx;
             praw[j] = raw;
             puv[j] = (unsigned)u | ((unsigned)vv << 16);
+            if (raw != 0u) pcache[j] = __ldcg(d.pxcache + idx);
             prgb[j] = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
           }
         }
@@ -476,11 +490,13 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
         for (int j = 0; j < kMaxPerThread; ++j) {
           // the next pixel's values rotate into slot 0 (registers, no local memory)
           const unsigned raw = praw[0], uvj = puv[0], rgbj = prgb[0];
+          const unsigned long long cj = pcache[0];
 #pragma unroll
           for (int r = 0; r + 1 < kMaxPerThread; ++r) {
             praw[r] = praw[r + 1];
             puv[r] = puv[r + 1];
             prgb[r] = prgb[r + 1];
+            pcache[r] = pcache[r + 1];
           }
           if (!pixel_valid(p, raw)) continue;
           const int u = (int)(uvj & 0xFFFFu), vv = (int)(uvj >> 16);
@@ -491,7 +507,10 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
           const float pz = R6 * x + R7 * y + R8 * D + t2;
           float V, gV[3], I, gI[3];
           bool colour;
-          if (!model_sample<ST>(d.v, p, px, py, pz, &V, gV, &I, gI, &colour)) continue;
+          unsigned long long fresh = kEmpty;
+          const bool found = model_sample<ST>(d.v, p, px, py, pz, &V, gV, &I, gI, &colour, cj, &fresh);
+          if (fresh != kEmpty) __stcg(d.pxcache + (size_t)vv * f.W + u, fresh);
+          if (!found) continue;
           const float Jd[6] = {gV[0], gV[1], gV[2], py * gV[2] - pz * gV[1], pz * gV[0] - px * gV[2],
                                px * gV[1] - py * gV[0]};
           add_jtj(acc, Jd, V, 1.0f);
@@ -629,6 +648,7 @@ RegDesc make_reg_desc(rf_volume* vol, const DevFrame& f, const double* T_init, c
   d.max_chunks = vol->max_chunks;
   d.bar = vol->d_regbar;
   d.status = vol->d_status;
+  d.pxcache = vol->d_pxcache;
   return d;
 }
 

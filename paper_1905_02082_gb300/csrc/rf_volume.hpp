@@ -57,6 +57,7 @@ struct rf_volume {
   rf_track_info* d_info = nullptr;
 
   unsigned* d_guard = nullptr;  // FP64 re-evaluated seed count of the last mask
+  unsigned long long* d_pxcache = nullptr;  // per pixel: block key << 22 | pool of its last sample
 
   // profiling: events recorded around the stages of the whole-frame calls
   bool profiling = false;
