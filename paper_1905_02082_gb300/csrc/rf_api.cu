@@ -494,6 +494,9 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
                                              offsetof(BatchStage, mode));
     desc[i] = make_reg_desc(v, f[i], v->d_T, nullptr, v->d_T + 16, nullptr);
     desc[n + i] = make_reg_desc(v, f[i], v->d_T + 16, v->d_mask, v->d_T + 32, v->d_info);
+    // no pixel block cache in batches: with many streams its traffic evicts
+    // the models from L2 (it changes no result)
+    desc[i].pxcache = desc[n + i].pxcache = nullptr;
   }
   e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
   if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);

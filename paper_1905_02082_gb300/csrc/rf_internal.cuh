@@ -119,7 +119,7 @@ struct RegDesc {
   unsigned* status;
   // per full-resolution pixel: the (block key << 22 | pool) its last sample
   // was found in, ~0 when none; a block's pool never changes until the
-  // volume is reset or imported, which clear the cache
+  // volume is reset or imported, which clear the cache.  nullptr: no cache
   unsigned long long* pxcache;
 };
 

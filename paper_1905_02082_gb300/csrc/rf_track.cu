@@ -482,7 +482,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
             const uint8_t* cp = f.rgb + 3 * (size_t)idx;
             praw[j] = raw;
             puv[j] = (unsigned)u | ((unsigned)vv << 16);
-            if (raw != 0u) pcache[j] = __ldcg(d.pxcache + idx);
+            if (raw != 0u && d.pxcache) pcache[j] = __ldcg(d.pxcache + idx);
             prgb[j] = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
           }
         }
@@ -509,7 +509,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
           bool colour;
           unsigned long long fresh = kEmpty;
           const bool found = model_sample<ST>(d.v, p, px, py, pz, &V, gV, &I, gI, &colour, cj, &fresh);
-          if (fresh != kEmpty) __stcg(d.pxcache + (size_t)vv * f.W + u, fresh);
+          if (fresh != kEmpty && d.pxcache) __stcg(d.pxcache + (size_t)vv * f.W + u, fresh);
           if (!found) continue;
           const float Jd[6] = {gV[0], gV[1], gV[2], py * gV[2] - pz * gV[1], pz * gV[0] - px * gV[2],
                                px * gV[1] - py * gV[0]};
