@@ -157,10 +157,15 @@ def run_serving(R, plan, clips, args):
                 for sp in run_specs]
         eng.run(warm, time_limit=120.0)
         eng.results.clear()
+        eng.batch_ms.clear()
         res = eng.run(run_specs, time_limit=300.0)
         summ = summarize(res)
         summ["peak_bytes"] = eng.stats["peak_bytes"]
         summ["batches"] = eng.stats["batches"]
+        if eng.batch_ms:
+            summ["batch_call_ms"] = {"p50": float(np.percentile(eng.batch_ms, 50)),
+                                     "max": float(np.max(eng.batch_ms)),
+                                     "over_20ms": int(np.sum(np.array(eng.batch_ms) > 20.0))}
         out[name] = summ
         eng.close()
     return out

@@ -144,6 +144,7 @@ class ServingEngine:
         self.used = 0
         self.cuda_stream = torch.cuda.Stream()
         self.results: List[FrameResult] = []
+        self.batch_ms: List[float] = []  # host time of each batch call, synchronised
         self.stats = {"slots_created": 0, "slots_destroyed": 0, "slot_reuses": 0, "evictions": 0, "restores": 0,
                       "batches": 0, "peak_bytes": 0}
 
@@ -273,9 +274,11 @@ class ServingEngine:
                 masks.append(None)
         if not ready:
             return 0
+        t_start = time.perf_counter()
         self.batch.process(frames, tin, tout, masks if self.keep_masks else None, self.cuda_stream)
         self.cuda_stream.synchronize()
         done = time.perf_counter() - self.t0
+        self.batch_ms.append(1000.0 * (time.perf_counter() - t_start))
         for st, m in ready:
             self._finish(st, done, m, len(ready))
         self.stats["batches"] += 1
@@ -295,6 +298,19 @@ class ServingEngine:
 
     # -- the loop ----------------------------------------------------------
     def run(self, specs: List[StreamSpec], time_limit: float = 600.0) -> List[FrameResult]:
+        """Serves the streams until every frame is done (garbage collection is
+        paused meanwhile, so that its pauses do not enter the latencies)."""
+        import gc
+        enabled = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._run(specs, time_limit)
+        finally:
+            if enabled:
+                gc.enable()
+
+    def _run(self, specs: List[StreamSpec], time_limit: float) -> List[FrameResult]:
         streams = [_Stream(s, self.dev) for s in specs]
         self.t0 = time.perf_counter()
         while True:
