@@ -138,7 +138,7 @@ template <class Alloc>
 rf_status volume_buffers(rf_volume* vol, const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width,
                          int max_height, Alloc&& A) {
   const size_t npix = (size_t)max_width * max_height;
-  const size_t max_chunks = (npix + 511) / 512;
+  const size_t max_chunks = (npix + 127) / 128;  // the smallest registration chunk
   const size_t ntiles = ((size_t)(max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
   const size_t nslots = (size_t)n_buckets * kSlots;
   rf_status s;
@@ -645,7 +645,7 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
     return s;
   }
   const size_t npix = (size_t)max_width * max_height;
-  vol->max_chunks = (int)((npix + 511) / 512);
+  vol->max_chunks = (int)((npix + 127) / 128);
   vol->reg_grid = register_max_grid(vol->device);
   if (vol->reg_grid > vol->sm_count) vol->reg_grid = vol->sm_count;
   if (vol->reg_grid < 1) {

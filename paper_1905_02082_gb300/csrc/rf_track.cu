@@ -399,9 +399,11 @@ constexpr int kRegThreads = 512;
 constexpr int kRegWarps = kRegThreads / 32;
 
 // Pixels per partial sum: a fixed chunk of the sampled pixels of a level
-// (512, or 2048 from 2^18 pixels), so the partials, and thus the result, do
-// not depend on how many CTAs run the registration.
-__device__ __forceinline__ int chunk_pixels(int npix) { return npix >= (1 << 18) ? 4 * kRegThreads : kRegThreads; }
+// (128 below 2^16 pixels, 512 below 2^18, else 2048), so the partials, and
+// thus the result, do not depend on how many CTAs run the registration.
+__device__ __forceinline__ int chunk_pixels(int npix) {
+  return npix >= (1 << 18) ? 4 * kRegThreads : (npix >= (1 << 16) ? kRegThreads : kRegThreads / 4);
+}
 constexpr int kMaxPerThread = 4;  // pixels of one chunk per thread (chunk_pixels / kRegThreads at most)
 
 // One whole registration (see the file comment) run by a group of G CTAs,
@@ -454,11 +456,17 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
       const float R0 = Tf[0], R1 = Tf[1], R2 = Tf[2], R3 = Tf[3], R4 = Tf[4], R5 = Tf[5], R6 = Tf[6], R7 = Tf[7],
                   R8 = Tf[8], t0 = Tf[9], t1 = Tf[10], t2 = Tf[11];
       float* part = d.partials + (size_t)(eval & 1) * 29 * d.max_chunks;
-      for (int ch = lb; ch < nchunks; ch += G) {
+      // chunks narrower than the CTA run side by side, one per warp group
+      // (slot): chunk lb + G (slot + slots it) at step it
+      const int width = min(chunk, kRegThreads);  // threads per chunk
+      const int slots = kRegThreads / width;
+      const int slot = threadIdx.x / width, tin = threadIdx.x % width;
+      for (int step = 0; lb + G * slots * step < nchunks; ++step) {
+        const int ch = lb + G * (slot + slots * step);
         float acc[29];
 #pragma unroll
         for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
-        const int end = min(npix, (ch + 1) * chunk);
+        const int end = ch < nchunks ? min(npix, (ch + 1) * chunk) : 0;
         // this thread's pixels of the chunk (at most kMaxPerThread): depth,
         // mask and colour loaded up front, so their latencies overlap; the
         // samples are then taken in the same order as the pixels
@@ -466,7 +474,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
         unsigned long long pcache[kMaxPerThread];
 #pragma unroll
         for (int j = 0; j < kMaxPerThread; ++j) {
-          const int i = ch * chunk + threadIdx.x + j * kRegThreads;
+          const int i = ch * chunk + tin + j * kRegThreads;
           praw[j] = 0u;
           puv[j] = 0u;
           prgb[j] = 0u;
@@ -542,11 +550,15 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
           if (lane < 29) red[warp][lane] = v[0];
         }
         __syncthreads();
-        if (threadIdx.x < 29) {
-          float sv = 0.0f;
-#pragma unroll
-          for (int w = 0; w < kRegWarps; ++w) sv += red[w][threadIdx.x];
-          part[threadIdx.x * nchunks + ch] = sv;
+        // the chunk partial of each slot: its warps' sums in order
+        if (warp < slots && lane < 29) {
+          const int cs = lb + G * (warp + slots * step);
+          if (cs < nchunks) {
+            const int wpc = width / 32;
+            float sv = 0.0f;
+            for (int w = 0; w < wpc; ++w) sv += red[warp * wpc + w][lane];
+            part[lane * nchunks + cs] = sv;
+          }
         }
         __syncthreads();
       }
