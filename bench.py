@@ -211,6 +211,9 @@ class ClockSampler:
 
 
 FLOPS_PER_SAMPLE = 320  # FP32 flops of one sampled pixel in one cost evaluation (depth + colour terms)
+# DRAM bytes (read + write) of one k_integrate launch on this workload, from the ncu capture summarised in
+# profiles/k_integrate_static_640x480.md (to be reset to None when the kernel changes)
+INTEGRATE_DRAM_BYTES = 37.697792e6 + 86.528e3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -616,7 +619,8 @@ def main():
                          "note": "latency-bound: dependent LM chain with a grid barrier per evaluation"},
             "roofline_integrate": {"bound": "hbm", "kernel": "k_integrate (per-voxel TSDF/colour update)",
                                    "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                                   "traffic": None, "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
+                                   "traffic": INTEGRATE_DRAM_BYTES,
+                                   "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch", "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
                                    "bytes_per_launch": statistics.mean(bytes_per),
                                    "launch_ms": statistics.mean(kern_ms)},
             "frame_hbm": {"achieved": frame_gbs, "peak": peak, "unit": "GB/s", "frac": frame_gbs / peak},

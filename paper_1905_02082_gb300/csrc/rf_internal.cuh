@@ -319,12 +319,17 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   return v;
 }
 
+// Arrival: one release reduction by thread 0 after the CTA barrier (it
+// orders the CTA's earlier writes before the count, without a full fence).
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_sync_counter(unsigned* count, unsigned target, unsigned* status) {
   __shared__ int s_ok2;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
+    red_release_gpu_add(count, 1u);
     int ok = 1;
     long long spins = 0;
     while (ld_acquire_gpu(count) < target) {
