@@ -302,16 +302,21 @@ rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coor
 rf_status rf_volume_stats(rf_volume* vol, rf_stats* out);
 
 /* Launch shapes of the kernels whose best grid depends on the device and the
- * workload: grid = number of SMs x CTAs per SM.  Defaults {16, 8, 2, 8}; the
+ * workload: grid = number of SMs x CTAs per SM, and the stream grouping of batched
+ * registrations.  Defaults {16, 8, 2, 8, 16}; the
  * package's autotuner (paper_1905_02082_gb300/autotune.py) measures them on
  * the current GPU and the Python binding applies its table.  Setting them
  * synchronises the device and drops the volume's captured graphs; batches
- * capture the shapes in force when they first see a frame shape. */
+ * capture the shapes in force (batch_group: the first volume's) when they
+ * first see a frame shape. */
 typedef struct rf_launch_config {
   int integrate_ctas_per_sm;  /* per-voxel update (k_integrate, 128 threads) */
   int cull_ctas_per_sm;       /* frustum block cull (256 threads) */
   int fixup_ctas_per_sm;      /* neighbour-table fixup (256 threads) */
   int raycast_ctas_per_sm;    /* virtual-depth ray casting (256 threads) */
+  int batch_group;            /* batches: tracked streams per registration launch at most, 0 = all in one
+                                 (smaller groups keep more of each launch's models in L2; on GB300 two
+                                 launches of 16 beat one of 32 by ~10 %) */
 } rf_launch_config;
 rf_status rf_get_launch_config(rf_volume* vol, rf_launch_config* out);
 rf_status rf_set_launch_config(rf_volume* vol, const rf_launch_config* cfg);

@@ -4,9 +4,10 @@
 
 Measures, on a seeded synthetic 640x480 sequence (the static room), the
 device time of the integration stage for each candidate grid of the
-per-voxel update, the frustum cull and the neighbour-table fixup, and of the
-virtual-depth ray casting for each candidate grid, one parameter after the
-other (coordinate descent from the library defaults).  Writes the winners to
+per-voxel update, the frustum cull and the neighbour-table fixup, of the
+virtual-depth ray casting for each candidate grid, and of a 32-stream batch
+for each registration grouping, one parameter after the other (coordinate
+descent from the library defaults).  Writes the winners to
 tuning/<device>_<SMs>sm.json, which Volume applies on creation.  Launch
 shapes change only the work distribution, never a result.
 """
@@ -30,7 +31,9 @@ CANDIDATES = {
     "cull_ctas_per_sm": (2, 4, 8, 16, 32),
     "fixup_ctas_per_sm": (1, 2, 4, 8),
     "raycast_ctas_per_sm": (2, 4, 8, 16, 32),
+    "batch_group": (16, 0, 32, 8, 4),
 }
+BATCH_STREAMS = 32  # streams of the batch used to tune batch_group
 
 
 def _frames(n: int):
@@ -90,6 +93,34 @@ def _raycast_ms(cfg, cam, dev_frames, poses, K, reps):
     return statistics.median(ms[reps:])
 
 
+def _batch_ms(cfg, cam, dev_frames, poses, K, reps):
+    """Mean device time of one rf_batch_process over BATCH_STREAMS volumes of
+    the same sequence (after 4 warm-up batches)."""
+    import torch
+    vols = [R.Volume(n_buckets=1 << 18, max_blocks=60_000, max_width=cam.width, max_height=cam.height,
+                     voxel_size=0.01, trunc=0.1, tune=False) for _ in range(BATCH_STREAMS)]
+    vols[0].set_launch_config(cfg)
+    batch = R.Batch(vols)
+    T = [poses[0].clone() for _ in vols]
+    Tn = [torch.empty_like(poses[0]) for _ in vols]
+    ms = []
+    n = min(len(dev_frames), 4 + 2 * reps)
+    for i in range(n):
+        fr = [v.frame(*dev_frames[i], K) for v in vols]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        batch.process(fr, T, Tn, None)
+        b.record()
+        b.synchronize()
+        T, Tn = Tn, T
+        if i >= 4:
+            ms.append(a.elapsed_time(b))
+    batch.close()
+    for v in vols:
+        v.close()
+    return statistics.mean(ms)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--frames", type=int, default=24)
@@ -105,7 +136,7 @@ def main(argv=None):
     dev_frames = [(torch.from_numpy(np.ascontiguousarray(d, dtype=np.uint16)).to(dev),
                    torch.from_numpy(np.ascontiguousarray(rgb)).to(dev)) for d, rgb, _, _ in frames]
     poses = [torch.as_tensor(T, device=dev).contiguous() for _, _, T, _ in frames]
-    cfg = R.rf_launch_config(16, 8, 2, 8)
+    cfg = R.rf_launch_config(16, 8, 2, 8, 16)
     defaults = {k: getattr(cfg, k) for k, _ in R.rf_launch_config._fields_}
     measured = {}
     t0 = time.time()
@@ -114,7 +145,7 @@ def main(argv=None):
         setattr(cfg, name, defaults[name])
         for v in cands:
             setattr(cfg, name, v)
-            f = _raycast_ms if name == "raycast_ctas_per_sm" else _integration_ms
+            f = {"raycast_ctas_per_sm": _raycast_ms, "batch_group": _batch_ms}.get(name, _integration_ms)
             times[v] = f(cfg, cam, dev_frames, poses, K, args.reps)
         # a candidate replaces the current value only when it is clearly faster
         # (differences within the run-to-run noise keep the default)
@@ -130,8 +161,9 @@ def main(argv=None):
     os.makedirs(os.path.dirname(out), exist_ok=True)
     table = {"device": prop.name, "sm_count": prop.multi_processor_count,
              "launch": {k: getattr(cfg, k) for k, _ in R.rf_launch_config._fields_},
-             "objective": "median device time of the integration stage (static room 640x480, 1 cm) and of "
-                          "virtual-depth ray casting; coordinate descent from the library defaults, a candidate "
+             "objective": "median device time of the integration stage (static room 640x480, 1 cm), of "
+                          "virtual-depth ray casting and of a 32-stream batch; coordinate descent from the library "
+                          "defaults, a candidate "
                           f"kept only when {100 * MIN_GAIN:.0f} % faster than the default",
              "measured_ms": measured, "seconds": round(time.time() - t0, 1)}
     with open(out, "w") as fh:

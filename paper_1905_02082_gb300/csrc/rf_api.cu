@@ -353,9 +353,13 @@ struct rf_batch_graph {
   std::vector<double> sig;  // per stream: H, W, fx, fy, cx, cy
   cudaGraphExec_t exec = nullptr;
   RegDesc* d_desc = nullptr;   // [2][n]: first and second registration
-  void* d_table = nullptr;     // [n] BatchStage, then CTA -> stream [total], then n + 1 group starts
+  // [n] BatchStage, then per registration launch (ngroups of them): CTA ->
+  // stream [total], then the n + 1 group starts
+  void* d_table = nullptr;
   std::vector<unsigned char> h_table;
   int total_ctas = 0;
+  int ngroups = 1;  // registration launches per registration
+  int gsize = 1;    // tracked streams per launch at most
 };
 
 struct rf_batch {
@@ -471,14 +475,21 @@ std::vector<int> split_ctas(const std::vector<double>& weight, int total) {
   return cnt;
 }
 
-size_t table_bytes(int n, int total_ctas) { return sizeof(BatchStage) * n + sizeof(int) * (total_ctas + n + 1); }
+size_t table_bytes(int n, int total_ctas, int ngroups) {
+  return sizeof(BatchStage) * n + sizeof(int) * (size_t)ngroups * (total_ctas + n + 1);
+}
 
 // Captures the batch graph for one shape.  Every stream gets the full path;
 // which streams actually track is decided per replay by the uploaded table.
 rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<double>& sig, rf_batch_graph* out) {
   const int n = (int)b->vols.size();
   out->total_ctas = b->vols[0]->reg_grid;
-  out->h_table.assign(table_bytes(n, out->total_ctas), 0);
+  // the tracked streams of a call run in groups of at most gsize per
+  // registration launch (launch setting batch_group; 0: all in one)
+  const int bg = b->vols[0]->launch.batch_group;
+  out->gsize = bg > 0 ? std::min(bg, n) : n;
+  out->ngroups = (n + out->gsize - 1) / out->gsize;
+  out->h_table.assign(table_bytes(n, out->total_ctas, out->ngroups), 0);
   cudaError_t e = cudaMalloc(&out->d_table, out->h_table.size());
   if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch table: ") + cudaGetErrorString(e));
   const void* out_table = out->d_table;
@@ -514,14 +525,16 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     s = batch_error(b, RF_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
   } else {
     const BatchStage* table = static_cast<const BatchStage*>(out->d_table);
-    const int* cta_stream = reinterpret_cast<const int*>(table + n);
-    const int* group_first = cta_stream + out->total_ctas;
+    const int* maps = reinterpret_cast<const int*>(table + n);
+    const int map_len = out->total_ctas + n + 1;
     int max_npix = 1;
     for (int i = 0; i < n; ++i) max_npix = std::max(max_npix, f[i].H * f[i].W);
     const dim3 copy_grid((unsigned)std::min((max_npix * 3 / 16 + 255) / 256, 64), (unsigned)n);
     k_batch_stage<<<copy_grid, 256, 0, cs>>>(table);
     for (int i = 0; i < n; ++i) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
-    s = launch_register_batch(b->vols[0], out->d_desc, cta_stream, group_first, out->total_ctas, cs);
+    for (int gi = 0; gi < out->ngroups && !s; ++gi)
+      s = launch_register_batch(b->vols[0], out->d_desc, maps + gi * map_len, maps + gi * map_len + out->total_ctas,
+                                out->total_ctas, cs);
     // residual seeds and erosion: concurrent; flood fills (cooperative): one at a time
     fork_aux(b, cs);
     for (int i = 0; i < n && !s; ++i)
@@ -533,7 +546,9 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
       s = launch_mask_post(b->vols[i], f[i], b->vols[i]->d_mask, b->aux[i % rf_batch::kAux]);
     join_aux(b, cs);
     for (int i = 0; i < n; ++i) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
-    if (!s) s = launch_register_batch(b->vols[0], out->d_desc + n, cta_stream, group_first, out->total_ctas, cs);
+    for (int gi = 0; gi < out->ngroups && !s; ++gi)
+      s = launch_register_batch(b->vols[0], out->d_desc + n, maps + gi * map_len,
+                                maps + gi * map_len + out->total_ctas, out->total_ctas, cs);
     // integrations: concurrent
     fork_aux(b, cs);
     for (int i = 0; i < n && !s; ++i)
@@ -974,6 +989,7 @@ rf_status rf_set_launch_config(rf_volume* vol, const rf_launch_config* cfg) {
                     cfg->raycast_ctas_per_sm};
   for (int x : v)
     if (x < 1 || x > 64) return set_error(vol, RF_ERR_INVALID_ARG, "CTAs per SM must be in 1..64");
+  if (cfg->batch_group < 0) return set_error(vol, RF_ERR_INVALID_ARG, "batch_group must be >= 0");
   rf_status s = check_cuda(vol, cudaDeviceSynchronize(), "launch config sync");
   if (s) return s;
   for (auto& g : vol->graphs) cudaGraphExecDestroy(g.exec);  // they hold the old shapes
@@ -1129,9 +1145,9 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
   }
   // per-call table: staging pointers and modes, then the registration CTA map
   BatchStage* tab = reinterpret_cast<BatchStage*>(g->h_table.data());
-  int* cta_stream = reinterpret_cast<int*>(tab + n);
-  int* group_first = cta_stream + g->total_ctas;
-  std::vector<double> w(n, 0.0);
+  int* maps = reinterpret_cast<int*>(tab + n);
+  const int map_len = g->total_ctas + n + 1;
+  std::vector<int> tracked;
   for (int i = 0; i < n; ++i) {
     rf_volume* v = b->vols[i];
     BatchStage& t = tab[i];
@@ -1146,16 +1162,25 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
     t.mask_buf = v->d_mask;
     t.npix = frames[i].height * frames[i].width;
     t.mode = mode[i];
-    if (mode[i] == kModeTrack) w[i] = (double)t.npix;
+    if (mode[i] == kModeTrack) tracked.push_back(i);
   }
-  const std::vector<int> cnt = split_ctas(w, g->total_ctas);
-  int c = 0;
-  for (int i = 0; i < n; ++i) {
-    group_first[i] = c;
-    for (int k = 0; k < cnt[i]; ++k) cta_stream[c++] = i;
+  // registration launch gi takes the tracked streams gi*gsize .. gi*gsize+gsize-1
+  // (in stream order), CTAs split among them by pixel count
+  for (int gi = 0; gi < g->ngroups; ++gi) {
+    int* cta_stream = maps + gi * map_len;
+    int* group_first = cta_stream + g->total_ctas;
+    std::vector<double> w(n, 0.0);
+    for (int k = gi * g->gsize; k < std::min((int)tracked.size(), (gi + 1) * g->gsize); ++k)
+      w[tracked[k]] = (double)tab[tracked[k]].npix;
+    const std::vector<int> cnt = split_ctas(w, g->total_ctas);
+    int c = 0;
+    for (int i = 0; i < n; ++i) {
+      group_first[i] = c;
+      for (int k = 0; k < cnt[i]; ++k) cta_stream[c++] = i;
+    }
+    group_first[n] = c;
+    for (; c < g->total_ctas; ++c) cta_stream[c] = -1;
   }
-  group_first[n] = c;
-  for (; c < g->total_ctas; ++c) cta_stream[c] = -1;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(g->d_table, g->h_table.data(), g->h_table.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, st);

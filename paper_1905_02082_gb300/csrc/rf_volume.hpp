@@ -64,7 +64,7 @@ struct rf_volume {
   cudaEvent_t ev[rf::EV_COUNT] = {};
 
   // launch shapes (grid = SMs x CTAs per SM), set by rf_set_launch_config
-  rf_launch_config launch = {16, 8, 2, 8};
+  rf_launch_config launch = {16, 8, 2, 8, 16};
 
   std::vector<rf_graph_entry> graphs;
   bool use_graphs = true;

@@ -65,7 +65,7 @@ class rf_profile(C.Structure):
 
 class rf_launch_config(C.Structure):
     _fields_ = [("integrate_ctas_per_sm", C.c_int), ("cull_ctas_per_sm", C.c_int), ("fixup_ctas_per_sm", C.c_int),
-                ("raycast_ctas_per_sm", C.c_int)]
+                ("raycast_ctas_per_sm", C.c_int), ("batch_group", C.c_int)]
 
 
 # (name, restype, argtypes) of every entry point of refusion.h
@@ -280,7 +280,9 @@ def tuned_launch_config(device=None) -> Optional[rf_launch_config]:
         if os.path.exists(path):
             import json
             d = json.load(open(path))["launch"]
-            cfg = rf_launch_config(**{k: int(d[k]) for k, _ in rf_launch_config._fields_})
+            defaults = {"integrate_ctas_per_sm": 16, "cull_ctas_per_sm": 8, "fixup_ctas_per_sm": 2,
+                        "raycast_ctas_per_sm": 8, "batch_group": 16}
+            cfg = rf_launch_config(**{k: int(d.get(k, defaults[k])) for k, _ in rf_launch_config._fields_})
         _tuned[path] = cfg
     return _tuned[path]
 

@@ -27,12 +27,12 @@ def test_launch_shapes_do_not_change_results(R):
     seq = make_sequence("tiny", 6)
     cam = seq.camera
     outs = []
-    for cfg in ((16, 8, 2, 8), (1, 1, 1, 1), (48, 32, 8, 32)):
+    for cfg in ((16, 8, 2, 8, 16), (1, 1, 1, 1, 1), (48, 32, 8, 32, 0)):
         vol = P.gpu_volume(R, cam, 0.02, tune=False)
         vol.set_launch_config(R.rf_launch_config(*cfg))
         got = vol.launch_config()
         assert (got.integrate_ctas_per_sm, got.cull_ctas_per_sm, got.fixup_ctas_per_sm,
-                got.raycast_ctas_per_sm) == cfg
+                got.raycast_ctas_per_sm, got.batch_group) == cfg
         T = None
         poses = []
         for i in range(len(seq)):
@@ -47,7 +47,7 @@ def test_launch_shapes_do_not_change_results(R):
         filled = vol.virtual_depth(P.dev_frame(R, vol, holes, rgb, cam), Tg).cpu().numpy()
         outs.append((np.array(poses), vol.export(), filled))
         with pytest.raises(R.RFError):
-            vol.set_launch_config(R.rf_launch_config(0, 8, 2, 8))
+            vol.set_launch_config(R.rf_launch_config(0, 8, 2, 8, 0))
         vol.close()
     for poses, snap, filled in outs[1:]:
         np.testing.assert_array_equal(poses, outs[0][0])

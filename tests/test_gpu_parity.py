@@ -397,10 +397,12 @@ def test_invalid_arguments(R):
 # batches of streams (one launch covers several uneven streams)
 # ---------------------------------------------------------------------------
 
-def test_batch_is_bit_identical_to_single_streams(R):
+@pytest.mark.parametrize("batch_group", [0, 2])
+def test_batch_is_bit_identical_to_single_streams(R, batch_group):
     """Three streams of different resolution, intrinsics and voxel size: the
     batched path gives exactly the poses, masks and volumes of the streams
-    processed alone (partial sums over fixed pixel chunks)."""
+    processed alone (partial sums over fixed pixel chunks), whether their
+    registrations share one launch or run in groups of two."""
     from synth.scenes import CAM_QVGA
     specs = [("tiny", 0, None, 0.02), ("dynamic", 1, CAM_QVGA, 0.03), ("static", 2, None, 0.01)]
     seqs = [make_sequence(c, sd, n_frames=4, camera=cam) for c, sd, cam, _ in specs]
@@ -408,6 +410,10 @@ def test_batch_is_bit_identical_to_single_streams(R):
     for mode in ("single", "batch"):
         vols = [gpu_volume(R, s.camera, vx, n_buckets=1 << 18, max_blocks=150000) for s, (_, _, _, vx) in
                 zip(seqs, specs)]
+        if mode == "batch":
+            cfg = vols[0].launch_config()
+            cfg.batch_group = batch_group
+            vols[0].set_launch_config(cfg)
         batch = R.Batch(vols) if mode == "batch" else None
         T = [None] * len(seqs)
         poses, masks = [], []
