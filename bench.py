@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import gc
 import json
 import multiprocessing as mp
 import os
@@ -564,7 +565,7 @@ def main():
                         voxel_size=VOXEL, trunc=TAU)
         h_depth = [torch.from_numpy(f[0]).pin_memory() for f in frames]
         h_rgb = [torch.from_numpy(f[1]).pin_memory() for f in frames]
-        Th = np.ascontiguousarray(frames[0][2])
+        Th = np.array(frames[0][2], dtype=np.float64)  # a copy: updated in place below
         To = np.zeros((4, 4))
         for w in range(args.warmup):
             i = order[w]
@@ -572,13 +573,17 @@ def main():
                                     None, stream)
             Th = To.copy()
         torch.cuda.synchronize()
+        hd = [h_depth[order[args.warmup + k]].numpy() for k in range(n_e2e)]
+        hc = [h_rgb[order[args.warmup + k]].numpy() for k in range(n_e2e)]
+        intr = [K.fx, K.fy, K.cx, K.cy]
+        gc.collect()
+        gc.disable()  # host-clocked: keep collector pauses out of the region
         t0 = time.perf_counter()
         for k in range(n_e2e):
-            i = order[args.warmup + k]
-            R.rf_process_frame_host(vol2.h, h_depth[i].numpy(), h_rgb[i].numpy(), [K.fx, K.fy, K.cx, K.cy], Th, To,
-                                    None, stream)
-            Th = To.copy()
+            R.rf_process_frame_host(vol2.h, hd[k], hc[k], intr, Th, To, None, stream)
+            Th[...] = To
         e2e_s = time.perf_counter() - t0
+        gc.enable()
         e2e = {"value": world * n_e2e / e2e_s, "unit": "frames/s",
                "h2d_bytes_per_step": cam.width * cam.height * 5 + 128, "d2h_bytes_per_step": 128,
                "steps": n_e2e, "api": "rf_process_frame_host"}
