@@ -466,7 +466,7 @@ def main():
 
     n_frames = min(args.warmup + args.steps, MAX_RENDERED)
     order = frame_order(n_frames, args.warmup + args.steps)
-    workers = min(16, os.cpu_count() or 1)
+    workers = max(1, min(16, (os.cpu_count() or 1) // world))  # ranks share the host cores
     frames = make_frames(seed=rank_seed(rank), n=n_frames, workers=workers)
     splan = serving_plan(args.serving_streams) if args.serving_streams > 0 and rank == 0 else []
     clips = render_serving_clips(splan, args.serving_clip, workers) if splan else []
