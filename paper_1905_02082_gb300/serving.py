@@ -24,7 +24,9 @@ memory (the host link of the GPU), so a frame's host-to-device transfer is
 part of the batch.
 
 mode="per_stream" serves the same arrivals with one rf_process_frame call per
-frame (the plain per-stream path) for comparison.
+frame (the plain per-stream path) for comparison.  In batch mode a lone ready
+frame also goes through rf_process_frame (single_when_alone): the result is
+the same, and the idle slots are not replayed with it.
 
 Latency of a frame = host clock when its batch (or call) has completed minus
 its arrival time.  This module is host-side scheduling only: every step of
@@ -127,7 +129,8 @@ class ServingEngine:
     """Serves StreamSpecs on the current CUDA device (see the module text)."""
 
     def __init__(self, budget_bytes: int, mode: str = "batch", max_slots: Optional[int] = None,
-                 evict_idle_s: float = 0.25, keep_masks: bool = False, export_final: bool = False):
+                 evict_idle_s: float = 0.25, keep_masks: bool = False, export_final: bool = False,
+                 single_when_alone: bool = True):
         import torch
         assert mode in ("batch", "per_stream")
         self.torch = torch
@@ -139,6 +142,9 @@ class ServingEngine:
         self.evict_idle_s = evict_idle_s
         self.keep_masks = keep_masks
         self.export_final = export_final
+        # a lone ready frame goes through rf_process_frame (same result, no
+        # idle slots replayed with it)
+        self.single_when_alone = single_when_alone
         self.slots: List[_Slot] = []
         self.batch: Optional[R.Batch] = None
         self.used = 0
@@ -255,6 +261,10 @@ class ServingEngine:
         return self.torch.empty(spec.height, spec.width, dtype=self.torch.uint8, device=self.dev)
 
     def _step_batch(self, now: float) -> int:
+        if self.single_when_alone:
+            alone = [slot.owner for slot in self.slots if slot.owner is not None and self._ready(slot.owner, now)]
+            if len(alone) == 1:
+                return self._step_per_stream(now, alone)
         frames, tin, tout, masks, ready = [], [], [], [], []
         for slot in self.slots:
             st = slot.owner
