@@ -99,6 +99,7 @@ __device__ __forceinline__ bool gated_off(const int* gate, int max_mode) {
 
 struct LMConst {
   double lambda0, eps_t, eps_r;
+  double eps_t2, eps_r2;  // squared, for the convergence test
   long long min_valid;
   int iters[3], strides[3];
 };

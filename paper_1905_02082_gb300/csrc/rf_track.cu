@@ -154,13 +154,48 @@ __device__ __forceinline__ void add_jtj(float* acc, const float J[6], float r, f
 }
 
 
+// float -> double conversions run on GB300's thin FP64 pipe; these build the
+// same values from the IEEE bit fields with integer operations.
+// Exact float -> double (normal numbers, zeros, infinities, NaN; a subnormal
+// float takes the converting instruction).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0u && (b & 0x7FFFFFu) != 0u) return (double)f;
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long ed = e == 0u ? 0ull : (e == 0xFFu ? 0x7FFull : (unsigned long long)(e - 127u + 1023u));
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
+// A float within 2^-20 (relative) of a double whose exponent is in the
+// normal float range; flags the other cases.
+__device__ __forceinline__ float d2f_approx(double d, bool* ok) {
+  const unsigned hi = (unsigned)(__double_as_longlong(d) >> 32);
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
+  *ok = e > -126 && e < 127;
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xFFFFFu) << 3));
+}
+
+// d > 0 and finite (no FP64 instruction): the bit pattern of a positive
+// finite double lies strictly between those of +0 and +infinity.
+__device__ __forceinline__ bool pos_finite(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0ll && b < 0x7FF0000000000000ll;
+}
+
+// For non-negative doubles the bit patterns order like the values.
+__device__ __forceinline__ bool nonneg_less(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+
 // FP64 reciprocal: FP32 seed refined by two FP64 Newton steps (relative
-// error ~(2^-23)^4, i.e. full double precision), far cheaper than a double
+// error ~(2^-20)^4, i.e. full double precision), far cheaper than a double
 // division on GB300's FP64 pipe.
 __device__ __forceinline__ double rcp_d(double d) {
-  const float df = (float)d;
-  if (!(fabsf(df) > 1e-36f && fabsf(df) < 1e36f)) return 1.0 / d;
-  double r = (double)__frcp_rn(df);
+  bool ok;
+  const float df = d2f_approx(d, &ok);
+  if (!ok) return 1.0 / d;
+  double r = f2d_exact(__frcp_rn(df));
   r = fma(fma(-d, r, 1.0), r, r);
   r = fma(fma(-d, r, 1.0), r, r);
   return r;
@@ -215,7 +250,7 @@ __device__ __forceinline__ double cofactor3(const double* a, int r, int c) {
 // Then the next candidate Tc = exp(d) T (FP64), with the se(3) exponential
 // R = I + A K + B K^2, t = (I + B K + C K^2) rho, K = [phi]x, K^2 = phi phi^T - th^2 I.
 __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const LMConst& c, int lane) {
-  if (lane < 29) S.red[lane] = (double)S.redf[lane];
+  if (lane < 29) S.red[lane] = f2d_exact(S.redf[lane]);
   __syncwarp();
   if (lane == 0) {
     const double En = S.red[27];
@@ -231,7 +266,7 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
       S.fin_N = Nn;
       S.done = Nn < c.min_valid ? 1 : 0;
       S.lambda = c.lambda0;
-    } else if (Nn >= c.min_valid && En * (double)S.N < S.E * (double)Nn) {
+    } else if (Nn >= c.min_valid && En * f2d_exact((float)S.N) < S.E * f2d_exact((float)Nn)) {  // N < 2^24: exact
       S.accept = 2;
       S.E = En;
       S.N = Nn;
@@ -273,7 +308,7 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
   }
   __syncwarp();
   const double detP = fma(A6[0], S.adjP[0], fma(A6[1], S.adjP[3], A6[2] * S.adjP[6]));
-  if (!(detP > 0.0) || !isfinite(detP) || !(A6[0] > 0.0)) {
+  if (!pos_finite(detP) || !pos_finite(A6[0])) {
     if (lane == 0) S.solve_ok = 0;
   } else {
     const double rP = rcp_d(detP);
@@ -305,7 +340,7 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
     }
     __syncwarp();
     const double detS = fma(S.Y[0], S.adjS[0], fma(S.Y[1], S.adjS[3], S.Y[2] * S.adjS[6]));
-    if (!(detS > 0.0) || !isfinite(detS) || !(S.Y[0] > 0.0)) {
+    if (!pos_finite(detS) || !pos_finite(S.Y[0])) {
       if (lane == 0) S.solve_ok = 0;
     } else {
       const double rS = rcp_d(detS);
@@ -326,9 +361,14 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
   }
   __syncwarp();
   const double d0 = S.d[0], d1 = S.d[1], d2 = S.d[2], w0 = S.d[3], w1 = S.d[4], w2 = S.d[5];
-  const double nr2 = fma(d0, d0, fma(d1, d1, d2 * d2));
-  const double th2 = fma(w0, w0, fma(w1, w1, w2 * w2));
-  if (!S.solve_ok || !isfinite(nr2 + th2)) {
+  // |rho|^2 on even lanes and |phi|^2 on odd lanes in one pass, then exchanged
+  const int o = (lane & 1) * 3;
+  const double sq = fma(S.d[o], S.d[o], fma(S.d[o + 1], S.d[o + 1], S.d[o + 2] * S.d[o + 2]));
+  const double sq_other = __shfl_xor_sync(0xffffffffu, sq, 1);
+  const double nr2 = (lane & 1) ? sq_other : sq;
+  const double th2 = (lane & 1) ? sq : sq_other;
+  const double inf = __longlong_as_double(0x7FF0000000000000ll);
+  if (!S.solve_ok || !nonneg_less(nr2, inf) || !nonneg_less(th2, inf)) {
     if (lane == 0) {
       S.info.converged[level] = 1;
       S.done = 1;
@@ -336,7 +376,7 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
     __syncwarp();
     return;
   }
-  if (nr2 < c.eps_t * c.eps_t && th2 < c.eps_r * c.eps_r) {
+  if (nonneg_less(nr2, c.eps_t2) && nonneg_less(th2, c.eps_r2)) {
     if (lane == 0) {
       S.info.converged[level] = 1;
       S.done = 1;
@@ -651,6 +691,8 @@ RegDesc make_reg_desc(rf_volume* vol, const DevFrame& f, const double* T_init, c
   d.c.lambda0 = vol->p.lm_lambda0;
   d.c.eps_t = vol->p.lm_eps_trans;
   d.c.eps_r = vol->p.lm_eps_rot;
+  d.c.eps_t2 = vol->p.lm_eps_trans * vol->p.lm_eps_trans;
+  d.c.eps_r2 = vol->p.lm_eps_rot * vol->p.lm_eps_rot;
   d.c.min_valid = vol->p.lm_min_valid;
   for (int l = 0; l < 3; ++l) {
     d.c.iters[l] = vol->p.lm_iters[l];
