@@ -353,6 +353,7 @@ struct rf_batch_graph {
   std::vector<double> sig;  // per stream: H, W, fx, fy, cx, cy
   cudaGraphExec_t exec = nullptr;
   RegDesc* d_desc = nullptr;   // [2][n]: first and second registration
+  FloodDesc* d_flood = nullptr;  // [n]: the flood fills
   // [n] BatchStage, then per registration launch (ngroups of them): CTA ->
   // stream [total], then the n + 1 group starts
   void* d_table = nullptr;
@@ -360,6 +361,7 @@ struct rf_batch_graph {
   int total_ctas = 0;
   int ngroups = 1;  // registration launches per registration
   int gsize = 1;    // tracked streams per launch at most
+  int ff_ctas = 0;  // CTAs of a batched flood-fill launch (its own maps follow the registration's)
 };
 
 struct rf_batch {
@@ -475,8 +477,22 @@ std::vector<int> split_ctas(const std::vector<double>& weight, int total) {
   return cnt;
 }
 
-size_t table_bytes(int n, int total_ctas, int ngroups) {
-  return sizeof(BatchStage) * n + sizeof(int) * (size_t)ngroups * (total_ctas + n + 1);
+size_t table_bytes(int n, int total_ctas, int ff_ctas, int ngroups) {
+  return sizeof(BatchStage) * n + sizeof(int) * (size_t)ngroups * ((total_ctas + n + 1) + (ff_ctas + n + 1));
+}
+
+// CTA map of one launch: the CTAs split among the streams of weight > 0.
+void fill_cta_map(const std::vector<double>& w, int total, int* cta_stream) {
+  const int n = (int)w.size();
+  int* group_first = cta_stream + total;
+  const std::vector<int> cnt = split_ctas(w, total);
+  int c = 0;
+  for (int i = 0; i < n; ++i) {
+    group_first[i] = c;
+    for (int k = 0; k < cnt[i]; ++k) cta_stream[c++] = i;
+  }
+  group_first[n] = c;
+  for (; c < total; ++c) cta_stream[c] = -1;
 }
 
 // Captures the batch graph for one shape.  Every stream gets the full path;
@@ -489,7 +505,8 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
   const int bg = b->vols[0]->launch.batch_group;
   out->gsize = bg > 0 ? std::min(bg, n) : n;
   out->ngroups = (n + out->gsize - 1) / out->gsize;
-  out->h_table.assign(table_bytes(n, out->total_ctas, out->ngroups), 0);
+  out->ff_ctas = b->vols[0]->ff_grid;
+  out->h_table.assign(table_bytes(n, out->total_ctas, out->ff_ctas, out->ngroups), 0);
   cudaError_t e = cudaMalloc(&out->d_table, out->h_table.size());
   if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch table: ") + cudaGetErrorString(e));
   const void* out_table = out->d_table;
@@ -509,8 +526,12 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     // the models from L2 (it changes no result)
     desc[i].pxcache = desc[n + i].pxcache = nullptr;
   }
+  std::vector<FloodDesc> flood(n);
+  for (int i = 0; i < n; ++i) flood[i] = make_flood_desc(b->vols[i], f[i]);
   e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
   if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&out->d_flood, sizeof(FloodDesc) * n);
+  if (e == cudaSuccess) e = cudaMemcpy(out->d_flood, flood.data(), sizeof(FloodDesc) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch descriptors: ") + cudaGetErrorString(e));
   std::vector<bool> prof(n);
   for (int i = 0; i < n; ++i) {
@@ -527,6 +548,8 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     const BatchStage* table = static_cast<const BatchStage*>(out->d_table);
     const int* maps = reinterpret_cast<const int*>(table + n);
     const int map_len = out->total_ctas + n + 1;
+    const int* ff_maps = maps + out->ngroups * map_len;
+    const int ff_len = out->ff_ctas + n + 1;
     int max_npix = 1;
     for (int i = 0; i < n; ++i) max_npix = std::max(max_npix, f[i].H * f[i].W);
     const dim3 copy_grid((unsigned)std::min((max_npix * 3 / 16 + 255) / 256, 64), (unsigned)n);
@@ -535,12 +558,15 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     for (int gi = 0; gi < out->ngroups && !s; ++gi)
       s = launch_register_batch(b->vols[0], out->d_desc, maps + gi * map_len, maps + gi * map_len + out->total_ctas,
                                 out->total_ctas, cs);
-    // residual seeds and erosion: concurrent; flood fills (cooperative): one at a time
+    // residual seeds and erosion: concurrent; flood fills: one cooperative
+    // launch per group of streams (the registration's CTA maps)
     fork_aux(b, cs);
     for (int i = 0; i < n && !s; ++i)
       s = launch_mask_pre(b->vols[i], f[i], b->vols[i]->d_T + 16, b->aux[i % rf_batch::kAux]);
     join_aux(b, cs);
-    for (int i = 0; i < n && !s; ++i) s = launch_mask_ff(b->vols[i], f[i], cs);
+    for (int gi = 0; gi < out->ngroups && !s; ++gi)
+      s = launch_floodfill_batch(b->vols[0], out->d_flood, ff_maps + gi * ff_len,
+                                 ff_maps + gi * ff_len + out->ff_ctas, out->ff_ctas, cs);
     fork_aux(b, cs);
     for (int i = 0; i < n && !s; ++i)
       s = launch_mask_post(b->vols[i], f[i], b->vols[i]->d_mask, b->aux[i % rf_batch::kAux]);
@@ -1097,6 +1123,7 @@ rf_status rf_batch_destroy(rf_batch* b) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.d_desc) cudaFree(g.d_desc);
     if (g.d_table) cudaFree(g.d_table);
+    if (g.d_flood) cudaFree(g.d_flood);
   }
   for (int k = 0; k < rf_batch::kAux; ++k) {
     if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
@@ -1139,6 +1166,7 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
       if (g->exec) cudaGraphExecDestroy(g->exec);
       if (g->d_desc) cudaFree(g->d_desc);
       if (g->d_table) cudaFree(g->d_table);
+      if (g->d_flood) cudaFree(g->d_flood);
       b->graphs.pop_back();
       return s;
     }
@@ -1147,6 +1175,8 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
   BatchStage* tab = reinterpret_cast<BatchStage*>(g->h_table.data());
   int* maps = reinterpret_cast<int*>(tab + n);
   const int map_len = g->total_ctas + n + 1;
+  int* ff_maps = maps + g->ngroups * map_len;
+  const int ff_len = g->ff_ctas + n + 1;
   std::vector<int> tracked;
   for (int i = 0; i < n; ++i) {
     rf_volume* v = b->vols[i];
@@ -1166,20 +1196,13 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
   }
   // registration launch gi takes the tracked streams gi*gsize .. gi*gsize+gsize-1
   // (in stream order), CTAs split among them by pixel count
+  // (the flood fills use the same groups, with maps over their own CTA count)
   for (int gi = 0; gi < g->ngroups; ++gi) {
-    int* cta_stream = maps + gi * map_len;
-    int* group_first = cta_stream + g->total_ctas;
     std::vector<double> w(n, 0.0);
     for (int k = gi * g->gsize; k < std::min((int)tracked.size(), (gi + 1) * g->gsize); ++k)
       w[tracked[k]] = (double)tab[tracked[k]].npix;
-    const std::vector<int> cnt = split_ctas(w, g->total_ctas);
-    int c = 0;
-    for (int i = 0; i < n; ++i) {
-      group_first[i] = c;
-      for (int k = 0; k < cnt[i]; ++k) cta_stream[c++] = i;
-    }
-    group_first[n] = c;
-    for (; c < g->total_ctas; ++c) cta_stream[c] = -1;
+    fill_cta_map(w, g->total_ctas, maps + gi * map_len);
+    fill_cta_map(w, g->ff_ctas, ff_maps + gi * ff_len);
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(g->d_table, g->h_table.data(), g->h_table.size(), cudaMemcpyHostToDevice, st);

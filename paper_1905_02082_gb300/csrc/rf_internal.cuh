@@ -375,6 +375,20 @@ rf_status launch_register_batch(rf_volume* vol, const RegDesc* descs, const int*
 // the three parts of launch_mask (the flood fill is the cooperative one)
 rf_status launch_mask_pre(rf_volume* vol, const DevFrame& f, const double* T, cudaStream_t st);
 rf_status launch_mask_ff(rf_volume* vol, const DevFrame& f, cudaStream_t st);
+// flood fills of several streams in one cooperative launch (the batches'
+// CTA maps; total_ctas must not exceed floodfill_max_grid)
+struct FloodDesc {
+  uint8_t* md;
+  const uint16_t* depth;
+  int H, W;
+  long long theta_ppm;
+  unsigned* ff;
+  int max_sweeps;
+  unsigned* status;
+};
+FloodDesc make_flood_desc(rf_volume* vol, const DevFrame& f);
+rf_status launch_floodfill_batch(rf_volume* vol, const FloodDesc* descs, const int* cta_stream, const int* first,
+                                 int total_ctas, cudaStream_t st);
 rf_status launch_mask_post(rf_volume* vol, const DevFrame& f, uint8_t* mask_out, cudaStream_t st);
 // neighbour tables of the blocks allocated since *lo_ptr (or since lo when lo_ptr is null)
 rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream_t st, const int* gate = nullptr);

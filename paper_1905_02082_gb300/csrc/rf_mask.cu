@@ -179,10 +179,9 @@ __device__ __forceinline__ bool ff_edge(unsigned Dsrc, unsigned Ddst, long long 
 }
 
 // ff words: [0] barrier count, [1] barrier generation, [2 + s] changed in sweep s
-__global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uint16_t* __restrict__ depth, int H,
-                                                           int W, long long theta_ppm, unsigned* ff, int max_sweeps,
-                                                           unsigned* status, const int* gate) {
-  if (gated_off(gate, kModeTrack)) return;  // uniform over the grid: before any barrier
+// Run by a group of G CTAs, this one being number lb of the group.
+__device__ void floodfill_body(uint8_t* md, const uint16_t* __restrict__ depth, int H, int W, long long theta_ppm,
+                               unsigned* ff, int max_sweeps, unsigned* status, int lb, int G) {
   __shared__ uint8_t sm[kFFH + 2][kFFW + 2];
   __shared__ uint16_t sd[kFFH + 2][kFFW + 2];
   const int tiles_x = (W + kFFW - 1) / kFFW, tiles_y = (H + kFFH - 1) / kFFH;
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uin
   unsigned* bar = ff;
   unsigned* changed = ff + 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tile = lb; tile < ntiles; tile += G) {
       const int u0 = (tile % tiles_x) * kFFW, v0 = (tile / tiles_x) * kFFH;
       // tile + 1-pixel halo into shared memory
       for (int i = threadIdx.x; i < (kFFH + 2) * (kFFW + 2); i += kFFThreads) {
@@ -223,10 +222,30 @@ __global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uin
       if (grew) md[v * W + u] = 1;
       if (__syncthreads_or(grew) && threadIdx.x == 0) atomicExch(changed + sweep, 1u);
     }
-    if (!grid_barrier(bar, gridDim.x, status)) return;
+    if (!grid_barrier(bar, G, status)) return;
     if (*(volatile unsigned*)(changed + sweep) == 0u) return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_NOT_CONVERGED);
+  if (lb == 0 && threadIdx.x == 0) atomicOr(status, ST_NOT_CONVERGED);
+}
+
+__global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uint16_t* __restrict__ depth, int H,
+                                                           int W, long long theta_ppm, unsigned* ff, int max_sweeps,
+                                                           unsigned* status, const int* gate) {
+  if (gated_off(gate, kModeTrack)) return;  // uniform over the grid: before any barrier
+  floodfill_body(md, depth, H, W, theta_ppm, ff, max_sweeps, status, blockIdx.x, gridDim.x);
+}
+
+// The flood fills of several streams in one cooperative launch: CTA b runs
+// stream cta_stream[b] (-1: none) as member b - first[s] of its group (the
+// CTA maps of the batched registration).  Groups never wait on each other.
+__global__ void __launch_bounds__(kFFThreads) k_floodfill_batch(const FloodDesc* __restrict__ descs,
+                                                                 const int* __restrict__ cta_stream,
+                                                                 const int* __restrict__ first) {
+  const int s = cta_stream[blockIdx.x];
+  if (s < 0) return;
+  const FloodDesc d = descs[s];
+  floodfill_body(d.md, d.depth, d.H, d.W, d.theta_ppm, d.ff, d.max_sweeps, d.status, blockIdx.x - first[s],
+                 first[s + 1] - first[s]);
 }
 
 }  // namespace
@@ -276,6 +295,34 @@ rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_
   if (s == RF_OK) s = launch_mask_ff(vol, f, st);
   if (s == RF_OK) s = launch_mask_post(vol, f, mask_out, st);
   return s;
+}
+
+FloodDesc make_flood_desc(rf_volume* vol, const DevFrame& f) {
+  FloodDesc d;
+  d.md = vol->d_md;
+  d.depth = f.depth;
+  d.H = f.H;
+  d.W = f.W;
+  d.theta_ppm = vol->dp.theta_ppm;
+  d.ff = vol->d_ff;
+  d.max_sweeps = vol->p.max_ff_sweeps;
+  d.status = vol->d_status;
+  return d;
+}
+
+rf_status launch_floodfill_batch(rf_volume* vol, const FloodDesc* descs, const int* cta_stream, const int* first,
+                                 int total_ctas, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(total_ctas);
+  cfg.blockDim = dim3(kFFThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return check_cuda(vol, cudaLaunchKernelEx(&cfg, k_floodfill_batch, descs, cta_stream, first),
+                    "batched flood-fill launch");
 }
 
 int floodfill_max_grid(int device) {
