@@ -275,6 +275,8 @@ rf_status enqueue_frame(rf_volume* vol, const DevFrame& f, bool first, cudaStrea
   return s;
 }
 
+constexpr size_t kMaxGraphs = 16;  // captured shapes kept per volume and per batch
+
 rf_status frame_graph(rf_volume* vol, const rf_frame* fr, bool first, cudaGraphExec_t* out) {
   for (const auto& g : vol->graphs)
     if (g.H == fr->height && g.W == fr->width && g.fx == fr->fx && g.fy == fr->fy && g.cx == fr->cx &&
@@ -307,7 +309,12 @@ rf_status frame_graph(rf_volume* vol, const rf_frame* fr, bool first, cudaGraphE
   ce = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if ((s = check_cuda(vol, ce, "graph instantiate"))) return s;
-  if (vol->graphs.size() >= 16) {
+  if (vol->graphs.size() >= kMaxGraphs) {
+    // the oldest shape goes; it may still be running (a rare event: wait)
+    if ((s = check_cuda(vol, cudaDeviceSynchronize(), "graph eviction sync"))) {
+      cudaGraphExecDestroy(exec);
+      return s;
+    }
     cudaGraphExecDestroy(vol->graphs.front().exec);
     vol->graphs.erase(vol->graphs.begin());
   }
@@ -1158,6 +1165,17 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
   rf_batch_graph* g = nullptr;
   for (auto& x : b->graphs)
     if (x.sig == sig) g = &x;
+  if (!g && b->graphs.size() >= kMaxGraphs) {
+    // the oldest shape goes; it may still be running (a rare event: wait)
+    cudaError_t se = cudaDeviceSynchronize();
+    if (se != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("graph eviction: ") + cudaGetErrorString(se));
+    rf_batch_graph& old = b->graphs.front();
+    if (old.exec) cudaGraphExecDestroy(old.exec);
+    if (old.d_desc) cudaFree(old.d_desc);
+    if (old.d_table) cudaFree(old.d_table);
+    if (old.d_flood) cudaFree(old.d_flood);
+    b->graphs.erase(b->graphs.begin());
+  }
   if (!g) {
     b->graphs.emplace_back();
     g = &b->graphs.back();

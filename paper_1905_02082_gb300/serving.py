@@ -130,15 +130,20 @@ class ServingEngine:
 
     def __init__(self, budget_bytes: int, mode: str = "batch", max_slots: Optional[int] = None,
                  evict_idle_s: float = 0.25, keep_masks: bool = False, export_final: bool = False,
-                 single_when_alone: bool = True):
+                 single_when_alone: bool = True, device=None):
         import torch
         assert mode in ("batch", "per_stream")
         self.torch = torch
         self.mode = mode
         self.budget = int(budget_bytes)
-        self.dev = torch.device("cuda", torch.cuda.current_device())
-        sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
-        self.max_slots = min(max_slots or sms, sms)
+        self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if self.dev.type == "cuda":
+            sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
+            self.max_slots = min(max_slots or sms, sms)  # a batch holds at most one stream per SM
+            self.cuda_stream = torch.cuda.Stream(self.dev)
+        else:  # host-only runs (the scheduling logic with a stand-in library)
+            self.max_slots = max_slots or 152
+            self.cuda_stream = None
         self.evict_idle_s = evict_idle_s
         self.keep_masks = keep_masks
         self.export_final = export_final
@@ -148,7 +153,6 @@ class ServingEngine:
         self.slots: List[_Slot] = []
         self.batch: Optional[R.Batch] = None
         self.used = 0
-        self.cuda_stream = torch.cuda.Stream()
         self.results: List[FrameResult] = []
         self.batch_ms: List[float] = []  # host time of each batch call, synchronised
         self.stats = {"slots_created": 0, "slots_destroyed": 0, "slot_reuses": 0, "evictions": 0, "restores": 0,
@@ -242,6 +246,10 @@ class ServingEngine:
         st.slot.owner = None
         st.slot = None
 
+    def _sync(self):
+        if self.cuda_stream is not None:
+            self.cuda_stream.synchronize()
+
     # -- one iteration -----------------------------------------------------
     def _ready(self, st: _Stream, now: float) -> bool:
         return st.slot is not None and not st.done and st.arrival(st.next) <= now
@@ -286,7 +294,7 @@ class ServingEngine:
             return 0
         t_start = time.perf_counter()
         self.batch.process(frames, tin, tout, masks if self.keep_masks else None, self.cuda_stream)
-        self.cuda_stream.synchronize()
+        self._sync()
         done = time.perf_counter() - self.t0
         self.batch_ms.append(1000.0 * (time.perf_counter() - t_start))
         for st, m in ready:
@@ -302,7 +310,7 @@ class ServingEngine:
             fr = R.make_frame(d, c, spec.K.fx, spec.K.fy, spec.K.cx, spec.K.cy)
             m = self._mask_for(spec)
             R.rf_process_frame(st.slot.vol.h, fr, st.pose, st.out, m, None, self.cuda_stream)
-            self.cuda_stream.synchronize()
+            self._sync()
             self._finish(st, time.perf_counter() - self.t0, m, 1)
         return len(ready)
 
