@@ -103,3 +103,11 @@ def test_volume_footprint_without_a_device(lib_path):
         R.rf_volume_footprint(p, 1000, 1000, 640, 480)  # buckets not a power of two
     with pytest.raises(R.RFError):
         R.rf_volume_footprint(p, 1 << 12, 0, 640, 480)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the built library the binding raises; it has no fallback."""
+    import paper_1905_02082_gb300.refusion as R
+    monkeypatch.setattr(R, "_lib", None)
+    with pytest.raises(ImportError):
+        R.load(str(tmp_path / "librefusion.so"))
