@@ -352,6 +352,9 @@ struct BatchStage {
   double* T_out;
   uint8_t* mask_out;  // nullable
   uint8_t* mask_buf;  // the volume's mask (zeroed for a first frame: nothing is masked)
+  unsigned* guard;    // the volume's seed guard count and flood-fill words, zeroed
+  unsigned* ff;       // for a tracked frame
+  int ff_words;
   int npix;
   int mode;  // kModeTrack, kModeFirst or kModeIdle; the gate of the stream's kernels
 };
@@ -361,6 +364,7 @@ struct rf_batch_graph {
   cudaGraphExec_t exec = nullptr;
   RegDesc* d_desc = nullptr;   // [2][n]: first and second registration
   FloodDesc* d_flood = nullptr;  // [n]: the flood fills
+  MaskDesc* d_mask = nullptr;    // [n]: seeds, erosion, dilation
   // [n] BatchStage, then per registration launch (ngroups of them): CTA ->
   // stream [total], then the n + 1 group starts
   void* d_table = nullptr;
@@ -418,6 +422,10 @@ __global__ void __launch_bounds__(256) k_batch_stage(const BatchStage* __restric
     copy_bytes(b.rgb_dst, b.rgb_src, (size_t)b.npix * 3, tid, nth);
   }
   if (b.mode == kModeFirst) zero_bytes(b.mask_buf, (size_t)b.npix, tid, nth);
+  if (b.mode == kModeTrack && blockIdx.x == 0) {
+    for (int k = threadIdx.x; k < b.ff_words; k += blockDim.x) b.ff[k] = 0u;
+    if (threadIdx.x == 0) *b.guard = 0u;
+  }
   if (blockIdx.x == 0 && threadIdx.x < 48) {
     const int k = threadIdx.x;
     if (k < 16 || b.mode != kModeTrack) b.T_dst[k] = b.T_src[k & 15];
@@ -435,6 +443,15 @@ __global__ void __launch_bounds__(256) k_batch_out(const BatchStage* __restrict_
 rf_status batch_error(rf_batch* b, rf_status s, const std::string& msg) {
   b->last_error = msg;
   return s;
+}
+
+// Releases a captured batch graph and its device descriptors (not running).
+void free_batch_graph(rf_batch_graph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  void* dev[] = {g.d_desc, g.d_table, g.d_flood, g.d_mask};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  g = rf_batch_graph();
 }
 
 // Fork: every auxiliary stream waits for the work enqueued on cs so far.
@@ -534,11 +551,18 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     desc[i].pxcache = desc[n + i].pxcache = nullptr;
   }
   std::vector<FloodDesc> flood(n);
-  for (int i = 0; i < n; ++i) flood[i] = make_flood_desc(b->vols[i], f[i]);
+  std::vector<MaskDesc> mdesc(n);
+  for (int i = 0; i < n; ++i) {
+    rf_volume* v = b->vols[i];
+    flood[i] = make_flood_desc(v, f[i]);
+    mdesc[i] = make_mask_desc(v, f[i], v->d_T + 16, v->d_mask);
+  }
   e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
   if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&out->d_flood, sizeof(FloodDesc) * n);
   if (e == cudaSuccess) e = cudaMemcpy(out->d_flood, flood.data(), sizeof(FloodDesc) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&out->d_mask, sizeof(MaskDesc) * n);
+  if (e == cudaSuccess) e = cudaMemcpy(out->d_mask, mdesc.data(), sizeof(MaskDesc) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("batch descriptors: ") + cudaGetErrorString(e));
   std::vector<bool> prof(n);
   for (int i = 0; i < n; ++i) {
@@ -565,24 +589,21 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     for (int gi = 0; gi < out->ngroups && !s; ++gi)
       s = launch_register_batch(b->vols[0], out->d_desc, maps + gi * map_len, maps + gi * map_len + out->total_ctas,
                                 out->total_ctas, cs);
-    // residual seeds and erosion: concurrent; flood fills: one cooperative
-    // launch per group of streams (the registration's CTA maps)
-    fork_aux(b, cs);
-    for (int i = 0; i < n && !s; ++i)
-      s = launch_mask_pre(b->vols[i], f[i], b->vols[i]->d_T + 16, b->aux[i % rf_batch::kAux]);
-    join_aux(b, cs);
+    // residual seeds and erosion of every stream: one launch each (guard
+    // counts and flood-fill words were reset by the staging kernel); flood
+    // fills: one cooperative launch per group of streams; dilation: one launch
+    if (!s) s = launch_mask_pre_batch(b->vols[0], out->d_mask, n, max_npix, cs);
     for (int gi = 0; gi < out->ngroups && !s; ++gi)
       s = launch_floodfill_batch(b->vols[0], out->d_flood, ff_maps + gi * ff_len,
                                  ff_maps + gi * ff_len + out->ff_ctas, out->ff_ctas, cs);
-    fork_aux(b, cs);
-    for (int i = 0; i < n && !s; ++i)
-      s = launch_mask_post(b->vols[i], f[i], b->vols[i]->d_mask, b->aux[i % rf_batch::kAux]);
-    join_aux(b, cs);
+    if (!s) s = launch_mask_post_batch(b->vols[0], out->d_mask, n, max_npix, cs);
     for (int i = 0; i < n; ++i) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
     for (int gi = 0; gi < out->ngroups && !s; ++gi)
       s = launch_register_batch(b->vols[0], out->d_desc + n, maps + gi * map_len,
                                 maps + gi * map_len + out->total_ctas, out->total_ctas, cs);
-    // integrations: concurrent
+    // integrations: concurrent (one launch over all streams' candidate
+    // blocks is no faster: the per-voxel update is latency-bound at its
+    // occupancy, and concurrent launches overlap the streams' frustum searches)
     fork_aux(b, cs);
     for (int i = 0; i < n && !s; ++i)
       s = launch_integrate(b->vols[i], f[i], b->vols[i]->d_T + 32, b->vols[i]->d_mask, b->aux[i % rf_batch::kAux]);
@@ -1127,10 +1148,7 @@ rf_status rf_batch_destroy(rf_batch* b) {
   if (!b) return RF_OK;
   cudaDeviceSynchronize();
   for (auto& g : b->graphs) {
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (g.d_desc) cudaFree(g.d_desc);
-    if (g.d_table) cudaFree(g.d_table);
-    if (g.d_flood) cudaFree(g.d_flood);
+    free_batch_graph(g);
   }
   for (int k = 0; k < rf_batch::kAux; ++k) {
     if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
@@ -1170,10 +1188,7 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
     cudaError_t se = cudaDeviceSynchronize();
     if (se != cudaSuccess) return batch_error(b, RF_ERR_CUDA, std::string("graph eviction: ") + cudaGetErrorString(se));
     rf_batch_graph& old = b->graphs.front();
-    if (old.exec) cudaGraphExecDestroy(old.exec);
-    if (old.d_desc) cudaFree(old.d_desc);
-    if (old.d_table) cudaFree(old.d_table);
-    if (old.d_flood) cudaFree(old.d_flood);
+    free_batch_graph(old);
     b->graphs.erase(b->graphs.begin());
   }
   if (!g) {
@@ -1181,10 +1196,7 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
     g = &b->graphs.back();
     rf_status s = batch_capture(b, frames, sig, g);
     if (s != RF_OK) {
-      if (g->exec) cudaGraphExecDestroy(g->exec);
-      if (g->d_desc) cudaFree(g->d_desc);
-      if (g->d_table) cudaFree(g->d_table);
-      if (g->d_flood) cudaFree(g->d_flood);
+      free_batch_graph(*g);
       b->graphs.pop_back();
       return s;
     }
@@ -1208,6 +1220,9 @@ rf_status rf_batch_process(rf_batch* b, const rf_frame* frames, const double* co
     t.T_out = T_out_dev[i];
     t.mask_out = mask_dev ? mask_dev[i] : nullptr;
     t.mask_buf = v->d_mask;
+    t.guard = v->d_guard;
+    t.ff = v->d_ff;
+    t.ff_words = 2 + v->p.max_ff_sweeps;
     t.npix = frames[i].height * frames[i].width;
     t.mode = mode[i];
     if (mode[i] == kModeTrack) tracked.push_back(i);

@@ -347,14 +347,196 @@ __device__ __forceinline__ unsigned colour_update(unsigned word, const uint8_t* 
   return out | (min(wc + 1, (unsigned)w_max) << 24);
 }
 
+// Per-lane constants of the voxel loop for one stream: lane l's offsets
+// within a block (from the quantised rotation) and the intrinsics in pixels.
+struct IntegConsts {
+  long long O[3], SY4[3], SZ[3];
+  float SY4f[3], SZf[3];
+  float fxg, fyg, cxg, cyg;
+};
+
+__device__ __forceinline__ void integ_consts(const long long* A, const DevFrame& f, const DevParams& p, int lane,
+                                             IntegConsts& c) {
+  const long long lx = (long long)(lane & 7) * p.v_um, ly = (long long)(lane >> 3) * p.v_um;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    c.O[i] = A[i * 3] * lx + A[i * 3 + 1] * ly;
+    c.SY4[i] = A[i * 3 + 1] * (4 * p.v_um);
+    c.SZ[i] = A[i * 3 + 2] * p.v_um;
+    c.SY4f[i] = (float)(c.SY4[i] >> 20);  // float estimates in ticks, converted once per thread
+    c.SZf[i] = (float)(c.SZ[i] >> 20);
+  }
+  c.fxg = (float)f.fxq * (1.0f / 256.0f);
+  c.fyg = (float)f.fyq * (1.0f / 256.0f);
+  c.cxg = (float)f.cxq * (1.0f / 256.0f);
+  c.cyg = (float)f.cyq * (1.0f / 256.0f);
+}
+
+// One candidate block b, integrated by one warp.  Lane l owns voxels
+// (x, y, z) = (l & 7, (l >> 3) + 4 (j & 1), j >> 1), j = 0..15, whose exact
+// camera coordinates follow from the block's by int64 additions.  (1) nearest
+// pixels of the 16 voxels (float estimate, exact integer path only near
+// rounding boundaries), (2) depth loads four at a time and the exact
+// truncation tests, (3) hash lookup (first bucket prefetched by lanes 0-3) or
+// insert, (4) read-modify-write of the updated voxels.  Per-voxel values are
+// staged in the warp's shared memory (spx, sx), not registers.  A and tq: the
+// quantised pose (shared memory).
+template <int ST>
+__device__ __forceinline__ void integrate_block(const DevVol& v, const DevFrame& f, const DevParams& p,
+                                                const uint8_t* __restrict__ mask, const long long* A,
+                                                const long long* tq, const IntegConsts& c, const int4 b, int lane,
+                                                int (*spx)[32], float (*sx)[32], unsigned& my_updated,
+                                                unsigned& my_new) {
+  const unsigned nan_bits = 0x7fc00000u;
+  const unsigned long long key = pack_key(b.x, b.y, b.z);
+  const bool in_range = coord_ok(b.x, b.y, b.z);
+  const unsigned long long bucket = bucket_of(key, v.bucket_mask);
+  unsigned long long e = kEmpty;
+  if (lane < kSlots && in_range) e = __ldcg(v.hash + bucket * kSlots + lane);  // prefetch
+  // exact camera coordinates of voxel (lane & 7, lane >> 3, 0) of this block
+  long long c0[3];
+  float c0f[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const long long d0 = (long long)b.x * 8 * p.v_um - tq[0], d1 = (long long)b.y * 8 * p.v_um - tq[1],
+                    d2 = (long long)b.z * 8 * p.v_um - tq[2];
+    c0[i] = A[i * 3] * d0 + A[i * 3 + 1] * d1 + A[i * 3 + 2] * d2 + c.O[i];
+    c0f[i] = (float)(c0[i] >> 20);
+  }
+  // 1) nearest pixel of each voxel
+#pragma unroll 2
+  for (int j = 0; j < kVPL; ++j) {
+    const int h = j & 1, zz = j >> 1;
+    const long long Cz = (c0[2] + (h ? c.SY4[2] : 0ll) + zz * c.SZ[2]) >> 20;
+    int pix = -1;
+    if (Cz > p.znear_tick && Cz <= p.dmax_tick) {
+      const float xf = c0f[0] + (h ? c.SY4f[0] : 0.0f) + (float)zz * c.SZf[0];
+      const float yf = c0f[1] + (h ? c.SY4f[1] : 0.0f) + (float)zz * c.SZf[1];
+      const float zf = c0f[2] + (h ? c.SY4f[2] : 0.0f) + (float)zz * c.SZf[2];
+      const float iz = __frcp_rn(zf);
+      const int u = pixel_fast(c.fxg * xf * iz + c.cxg, f.amb_u, f.W);
+      const int vv = pixel_fast(c.fyg * yf * iz + c.cyg, f.amb_v, f.H);
+      pix = (u == kAmbiguous || vv == kAmbiguous) ? kAmbiguous : ((u < 0 || vv < 0) ? -1 : vv * f.W + u);
+      if (pix == kAmbiguous) {
+        const long long Cx = (c0[0] + (h ? c.SY4[0] : 0ll) + zz * c.SZ[0]) >> 20;
+        const long long Cy = (c0[1] + (h ? c.SY4[1] : 0ll) + zz * c.SZ[1]) >> 20;
+        pix = voxel_pixel(Cx, Cy, Cz, xf, yf, zf, f, p, c.fxg, c.fyg, c.cxg, c.cyg);
+      }
+    }
+    spx[j][lane] = pix;
+  }
+  // 2) depth (and mask) loads, four voxels at a time, and the exact tests
+  unsigned passbits = 0;
+#pragma unroll 4
+  for (int j = 0; j < kVPL; ++j) {
+    const int pix = spx[j][lane];
+    unsigned raw = pix >= 0 ? (unsigned)__ldg(f.depth + pix) : 0u;
+    if (mask && pix >= 0 && __ldg(mask + pix)) raw = 0u;  // masked pixel: as invalid
+    const int h = j & 1, zz = j >> 1;
+    const long long Cz = (c0[2] + (h ? c.SY4[2] : 0ll) + zz * c.SZ[2]) >> 20;
+    float x = 0.0f;
+    bool band = false;
+    const bool ok = pix >= 0 && voxel_value(raw, Cz, p, &x, &band);
+    sx[j][lane] = x;
+    if (band) spx[j][lane] = pix | (int)0x80000000;
+    passbits |= ok ? (1u << j) : 0u;
+  }
+  if (!__any_sync(0xffffffffu, passbits != 0)) return;
+  // 3) pool index: from the prefetched bucket, else probe/insert by lane 0
+  const unsigned found = __ballot_sync(0xffffffffu, lane < kSlots && e != kEmpty && (e >> 22) == key);
+  int pool;
+  bool fresh = false;
+  if (found) {
+    pool = (int)(__shfl_sync(0xffffffffu, e, __ffs(found) - 1) & 0x3FFFFFull);
+  } else {
+    int pl = -1, nw = 0;
+    if (lane == 0) {
+      bool is_new;
+      pl = hash_insert(v, b.x, b.y, b.z, &is_new);
+      nw = is_new;
+    }
+    pool = __shfl_sync(0xffffffffu, pl, 0);
+    fresh = __shfl_sync(0xffffffffu, nw, 0) != 0;
+  }
+  if (pool < 0) return;
+  my_new += (lane == 0 && fresh) ? 1u : 0u;
+  my_updated += __popc(passbits);
+  if constexpr (ST == RF_STORAGE_FP32) {
+    uint2* vb = v.vox + (size_t)pool * kBV + lane;
+    uint8_t* wb = v.W + (size_t)pool * kBV + lane;
+    // 4) read-modify-write
+#pragma unroll 4
+    for (int j = 0; j < kVPL; ++j) {
+      const bool pass = (passbits >> j) & 1u;
+      uint2 w;
+      unsigned W;
+      if (fresh) {
+        w = make_uint2(nan_bits, 0u);
+        W = 0;
+      } else {
+        if (!pass) continue;
+        w = vb[32 * j];
+        W = wb[32 * j];
+      }
+      if (pass) {
+        const float F = __uint_as_float(w.x);
+        const float x = sx[j][lane];
+        const int px = spx[j][lane];
+        const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
+        w.x = __float_as_uint(Fn);
+        if (px < 0) w.y = colour_update(w.y, f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);  // band
+        W = min(W + 1, (unsigned)p.w_max);
+      }
+      vb[32 * j] = w;
+      wb[32 * j] = (uint8_t)W;
+    }
+  } else {
+    // FP16 storage: the tracking word always, the colour word inside the band
+    unsigned* tb = trk_words_rw(v, pool) + lane;
+    unsigned* cb = tb + kBV;
+#pragma unroll 4
+    for (int j = 0; j < kVPL; ++j) {
+      const bool pass = (passbits >> j) & 1u;
+      unsigned t;
+      if (fresh) {
+        t = kTrkEmpty;
+      } else {
+        if (!pass) continue;
+        t = tb[32 * j];
+      }
+      unsigned col = 0u;
+      bool col_written = fresh;
+      if (pass) {
+        const unsigned W = t >> 24;
+        const float x = sx[j][lane];
+        const int px = spx[j][lane];
+        const float F = __half2float(__ushort_as_half((unsigned short)(t & 0xFFFFu))) * p.tau;
+        const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
+        const unsigned h = (unsigned)__half_as_ushort(__float2half_rn(Fn * p.inv_tau));
+        unsigned i8 = (t >> 16) & 255u;
+        if (px < 0) {  // band: colour, and the intensity derived from it
+          col = colour_update(fresh ? 0u : cb[32 * j], f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);
+          col_written = true;
+          i8 = rgb_i8(col);
+        }
+        t = h | (i8 << 16) | (min(W + 1, (unsigned)p.w_max) << 24);
+      }
+      tb[32 * j] = t;
+      if (col_written) cb[32 * j] = col;
+    }
+  }
+}
+
+// Counts of one warp for one stream's integration statistics.
+__device__ __forceinline__ void integ_flush(IntegState* st, unsigned updated, unsigned fresh, int lane) {
+  updated = __reduce_add_sync(0xffffffffu, updated);
+  fresh = __reduce_add_sync(0xffffffffu, fresh);
+  if (lane == 0 && updated) atomicAdd(&st->updated, (unsigned long long)updated);
+  if (lane == 0 && fresh) atomicAdd(&st->new_blocks, (int)fresh);
+}
+
 // One warp per candidate block (static round-robin over all warps): no CTA
-// barriers.  Lane l owns voxels (x, y, z) = (l & 7, (l >> 3) + 4 (j & 1), j >> 1),
-// j = 0..15, whose exact camera coordinates follow from the block's by int64
-// additions.  Per block: (1) nearest pixels of the 16 voxels (float estimate,
-// exact integer path only near rounding boundaries), (2) depth loads four at
-// a time and the exact truncation tests, (3) hash lookup (first bucket
-// prefetched by lanes 0-3) or insert, (4) read-modify-write of the updated
-// voxels.  Per-voxel values are staged in shared memory, not registers.
+// barriers.
 template <int ST>
 __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame f, DevParams p,
                                                              const uint8_t* __restrict__ mask, IntegState* st,
@@ -364,200 +546,47 @@ __global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame 
   __shared__ long long A[9], tq[3];              // quantised pose
   if (gated_off(f.gate, kModeFirst)) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int(*spx)[32] = s_px[wid];
-  float(*sx)[32] = s_x[wid];
   if (threadIdx.x < 9) A[threadIdx.x] = st->A[threadIdx.x];
   if (threadIdx.x < 3) tq[threadIdx.x] = st->tq[threadIdx.x];
   __syncthreads();
   const long long n_cand = min((long long)*(volatile int*)&st->n_cand, max_cand);
-  const long long lx = (long long)(lane & 7) * p.v_um, ly = (long long)(lane >> 3) * p.v_um;
-  long long O[3], SY4[3], SZ[3];
-  float SY4f[3], SZf[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    O[i] = A[i * 3] * lx + A[i * 3 + 1] * ly;
-    SY4[i] = A[i * 3 + 1] * (4 * p.v_um);
-    SZ[i] = A[i * 3 + 2] * p.v_um;
-    SY4f[i] = (float)(SY4[i] >> 20);  // float estimates in ticks, converted once per thread
-    SZf[i] = (float)(SZ[i] >> 20);
-  }
-  const float fxg = (float)f.fxq * (1.0f / 256.0f), fyg = (float)f.fyq * (1.0f / 256.0f);
-  const float cxg = (float)f.cxq * (1.0f / 256.0f), cyg = (float)f.cyq * (1.0f / 256.0f);
-  const unsigned nan_bits = 0x7fc00000u;
+  IntegConsts c;
+  integ_consts(A, f, p, lane, c);
   const long long warp0 = ((long long)blockIdx.x * kIntegThreads + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * kIntegThreads) >> 5;
   unsigned my_updated = 0, my_new = 0;
-  for (long long ci = warp0; ci < n_cand; ci += nwarps) {
-    const int4 b = cand[ci];
-    const unsigned long long key = pack_key(b.x, b.y, b.z);
-    const bool in_range = coord_ok(b.x, b.y, b.z);
-    const unsigned long long bucket = bucket_of(key, v.bucket_mask);
-    unsigned long long e = kEmpty;
-    if (lane < kSlots && in_range) e = __ldcg(v.hash + bucket * kSlots + lane);  // prefetch
-    // exact camera coordinates of voxel (lane & 7, lane >> 3, 0) of this block
-    long long c0[3];
-    float c0f[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const long long d0 = (long long)b.x * 8 * p.v_um - tq[0], d1 = (long long)b.y * 8 * p.v_um - tq[1],
-                      d2 = (long long)b.z * 8 * p.v_um - tq[2];
-      c0[i] = A[i * 3] * d0 + A[i * 3 + 1] * d1 + A[i * 3 + 2] * d2 + O[i];
-      c0f[i] = (float)(c0[i] >> 20);
-    }
-    // 1) nearest pixel of each voxel
-#pragma unroll 2
-    for (int j = 0; j < kVPL; ++j) {
-      const int h = j & 1, zz = j >> 1;
-      const long long Cz = (c0[2] + (h ? SY4[2] : 0ll) + zz * SZ[2]) >> 20;
-      int pix = -1;
-      if (Cz > p.znear_tick && Cz <= p.dmax_tick) {
-        const float xf = c0f[0] + (h ? SY4f[0] : 0.0f) + (float)zz * SZf[0];
-        const float yf = c0f[1] + (h ? SY4f[1] : 0.0f) + (float)zz * SZf[1];
-        const float zf = c0f[2] + (h ? SY4f[2] : 0.0f) + (float)zz * SZf[2];
-        const float iz = __frcp_rn(zf);
-        const int u = pixel_fast(fxg * xf * iz + cxg, f.amb_u, f.W);
-        const int vv = pixel_fast(fyg * yf * iz + cyg, f.amb_v, f.H);
-        pix = (u == kAmbiguous || vv == kAmbiguous) ? kAmbiguous : ((u < 0 || vv < 0) ? -1 : vv * f.W + u);
-        if (pix == kAmbiguous) {
-          const long long Cx = (c0[0] + (h ? SY4[0] : 0ll) + zz * SZ[0]) >> 20;
-          const long long Cy = (c0[1] + (h ? SY4[1] : 0ll) + zz * SZ[1]) >> 20;
-          pix = voxel_pixel(Cx, Cy, Cz, xf, yf, zf, f, p, fxg, fyg, cxg, cyg);
-        }
-      }
-      spx[j][lane] = pix;
-    }
-    // 2) depth (and mask) loads, four voxels at a time, and the exact tests
-    unsigned passbits = 0;
-#pragma unroll 4
-    for (int j = 0; j < kVPL; ++j) {
-      const int pix = spx[j][lane];
-      unsigned raw = pix >= 0 ? (unsigned)__ldg(f.depth + pix) : 0u;
-      if (mask && pix >= 0 && __ldg(mask + pix)) raw = 0u;  // masked pixel: as invalid
-      const int h = j & 1, zz = j >> 1;
-      const long long Cz = (c0[2] + (h ? SY4[2] : 0ll) + zz * SZ[2]) >> 20;
-      float x = 0.0f;
-      bool band = false;
-      const bool ok = pix >= 0 && voxel_value(raw, Cz, p, &x, &band);
-      sx[j][lane] = x;
-      if (band) spx[j][lane] = pix | (int)0x80000000;
-      passbits |= ok ? (1u << j) : 0u;
-    }
-    if (!__any_sync(0xffffffffu, passbits != 0)) continue;
-    // 3) pool index: from the prefetched bucket, else probe/insert by lane 0
-    const unsigned found = __ballot_sync(0xffffffffu, lane < kSlots && e != kEmpty && (e >> 22) == key);
-    int pool;
-    bool fresh = false;
-    if (found) {
-      pool = (int)(__shfl_sync(0xffffffffu, e, __ffs(found) - 1) & 0x3FFFFFull);
-    } else {
-      int pl = -1, nw = 0;
-      if (lane == 0) {
-        bool is_new;
-        pl = hash_insert(v, b.x, b.y, b.z, &is_new);
-        nw = is_new;
-      }
-      pool = __shfl_sync(0xffffffffu, pl, 0);
-      fresh = __shfl_sync(0xffffffffu, nw, 0) != 0;
-    }
-    if (pool < 0) continue;
-    my_new += (lane == 0 && fresh) ? 1u : 0u;
-    my_updated += __popc(passbits);
-    if constexpr (ST == RF_STORAGE_FP32) {
-      uint2* vb = v.vox + (size_t)pool * kBV + lane;
-      uint8_t* wb = v.W + (size_t)pool * kBV + lane;
-      // 4) read-modify-write
-#pragma unroll 4
-      for (int j = 0; j < kVPL; ++j) {
-        const bool pass = (passbits >> j) & 1u;
-        uint2 w;
-        unsigned W;
-        if (fresh) {
-          w = make_uint2(nan_bits, 0u);
-          W = 0;
-        } else {
-          if (!pass) continue;
-          w = vb[32 * j];
-          W = wb[32 * j];
-        }
-        if (pass) {
-          const float F = __uint_as_float(w.x);
-          const float x = sx[j][lane];
-          const int px = spx[j][lane];
-          const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
-          w.x = __float_as_uint(Fn);
-          if (px < 0) w.y = colour_update(w.y, f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);  // band
-          W = min(W + 1, (unsigned)p.w_max);
-        }
-        vb[32 * j] = w;
-        wb[32 * j] = (uint8_t)W;
-      }
-    } else {
-      // FP16 storage: the tracking word always, the colour word inside the band
-      unsigned* tb = trk_words_rw(v, pool) + lane;
-      unsigned* cb = tb + kBV;
-#pragma unroll 4
-      for (int j = 0; j < kVPL; ++j) {
-        const bool pass = (passbits >> j) & 1u;
-        unsigned t;
-        if (fresh) {
-          t = kTrkEmpty;
-        } else {
-          if (!pass) continue;
-          t = tb[32 * j];
-        }
-        unsigned col = 0u;
-        bool col_written = fresh;
-        if (pass) {
-          const unsigned W = t >> 24;
-          const float x = sx[j][lane];
-          const int px = spx[j][lane];
-          const float F = __half2float(__ushort_as_half((unsigned short)(t & 0xFFFFu))) * p.tau;
-          const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
-          const unsigned h = (unsigned)__half_as_ushort(__float2half_rn(Fn * p.inv_tau));
-          unsigned i8 = (t >> 16) & 255u;
-          if (px < 0) {  // band: colour, and the intensity derived from it
-            col = colour_update(fresh ? 0u : cb[32 * j], f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);
-            col_written = true;
-            i8 = rgb_i8(col);
-          }
-          t = h | (i8 << 16) | (min(W + 1, (unsigned)p.w_max) << 24);
-        }
-        tb[32 * j] = t;
-        if (col_written) cb[32 * j] = col;
-      }
-    }
-  }
-  my_updated = __reduce_add_sync(0xffffffffu, my_updated);
-  my_new = __reduce_add_sync(0xffffffffu, my_new);
-  if (lane == 0 && my_updated) atomicAdd(&st->updated, (unsigned long long)my_updated);
-  if (lane == 0 && my_new) atomicAdd(&st->new_blocks, (int)my_new);
+  for (long long ci = warp0; ci < n_cand; ci += nwarps)
+    integrate_block<ST>(v, f, p, mask, A, tq, c, cand[ci], lane, s_px[wid], s_x[wid], my_updated, my_new);
+  integ_flush(st, my_updated, my_new, lane);
 }
 
 // Neighbour tables of the blocks allocated since `lo`: each new block gets
 // the pools of its 7 positive neighbours, and each existing negative
 // neighbour gets the new block in the matching slot.  Runs after the
 // integration (the hash is complete and read-only here).
+__device__ __forceinline__ void fixup_block(const DevVol& v, int b) {
+  const int4 c = v.coords[b];
+  if (c.w == 0) return;
+  int* flat = reinterpret_cast<int*>(v.nbr);
+  int t[8];
+  t[0] = b;
+#pragma unroll
+  for (int o = 1; o < 8; ++o) t[o] = hash_find(v, c.x + (o & 1), c.y + ((o >> 1) & 1), c.z + ((o >> 2) & 1));
+  v.nbr[2 * (size_t)b] = make_int4(t[0], t[1], t[2], t[3]);
+  v.nbr[2 * (size_t)b + 1] = make_int4(t[4], t[5], t[6], t[7]);
+#pragma unroll
+  for (int o = 1; o < 8; ++o) {
+    const int n = hash_find(v, c.x - (o & 1), c.y - ((o >> 1) & 1), c.z - ((o >> 2) & 1));
+    if (n >= 0) flat[8 * (size_t)n + o] = b;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_nbr_fixup(DevVol v, const int* __restrict__ lo_ptr, int lo_value,
                                                    const int* gate) {
   if (gated_off(gate, kModeFirst)) return;
   const int lo = lo_ptr ? *lo_ptr : lo_value;
   const int hi = min(*(volatile int*)v.n_blocks, v.max_blocks);
-  int* flat = reinterpret_cast<int*>(v.nbr);
-  for (int b = lo + blockIdx.x * blockDim.x + threadIdx.x; b < hi; b += gridDim.x * blockDim.x) {
-    const int4 c = v.coords[b];
-    if (c.w == 0) continue;
-    int t[8];
-    t[0] = b;
-#pragma unroll
-    for (int o = 1; o < 8; ++o) t[o] = hash_find(v, c.x + (o & 1), c.y + ((o >> 1) & 1), c.z + ((o >> 2) & 1));
-    v.nbr[2 * (size_t)b] = make_int4(t[0], t[1], t[2], t[3]);
-    v.nbr[2 * (size_t)b + 1] = make_int4(t[4], t[5], t[6], t[7]);
-#pragma unroll
-    for (int o = 1; o < 8; ++o) {
-      const int n = hash_find(v, c.x - (o & 1), c.y - ((o >> 1) & 1), c.z - ((o >> 2) & 1));
-      if (n >= 0) flat[8 * (size_t)n + o] = b;
-    }
-  }
+  for (int b = lo + blockIdx.x * blockDim.x + threadIdx.x; b < hi; b += gridDim.x * blockDim.x) fixup_block(v, b);
 }
 
 }  // namespace
@@ -567,13 +596,20 @@ rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream
   return check_cuda(vol, cudaGetLastError(), "neighbour table launch");
 }
 
-rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st) {
+// The frustum search of an integration: prep, tile maxima, AABB, cull.
+static rf_status launch_frustum(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st) {
   const int tiles_x = (f.W + kTile - 1) / kTile, tiles_y = (f.H + kTile - 1) / kTile;
   k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks, f.gate);
   k_tilemax<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x);
   k_integ_aabb<<<1, 32, 0, st>>>(T, f, vol->dp, vol->d_integ);
   k_cull<<<vol->sm_count * vol->launch.cull_ctas_per_sm, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
                                             vol->p.max_candidates, vol->d_status);
+  return check_cuda(vol, cudaGetLastError(), "frustum launch");
+}
+
+rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st) {
+  rf_status s = launch_frustum(vol, f, T, mask, st);
+  if (s != RF_OK) return s;
   prof_record(vol, EV_KERNEL0, st);
   if (vol->p.storage == RF_STORAGE_FP16)
     k_integrate<RF_STORAGE_FP16><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
@@ -582,7 +618,7 @@ rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, c
     k_integrate<RF_STORAGE_FP32><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
                                                                              vol->d_cand, vol->p.max_candidates);
   prof_record(vol, EV_KERNEL1, st);
-  rf_status s = check_cuda(vol, cudaGetLastError(), "integrate launch");
+  s = check_cuda(vol, cudaGetLastError(), "integrate launch");
   if (s != RF_OK) return s;
   return launch_nbr_fixup(vol, &vol->d_integ->pool_before, 0, st, f.gate);
 }

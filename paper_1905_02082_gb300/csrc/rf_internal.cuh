@@ -142,6 +142,18 @@ struct IntegState {
   unsigned long long updated;
 };
 
+// Everything one stream's residual seeds, erosion and dilation need.
+struct MaskDesc {
+  DevVol v;
+  DevFrame f;
+  DevParams p;
+  const double* T;  // first-registration pose
+  uint8_t* seeds;
+  unsigned* guard;
+  uint8_t* md;
+  uint8_t* mask_out;
+};
+
 __device__ __forceinline__ bool coord_ok(int bx, int by, int bz) {
   return bx >= -kMaxCoord && bx <= kMaxCoord && by >= -kMaxCoord && by <= kMaxCoord && bz >= -kMaxCoord &&
          bz <= kMaxCoord;
@@ -363,6 +375,12 @@ rf_status launch_mask(rf_volume* vol, const DevFrame& f, const double* T, uint8_
 rf_status launch_virtual_depth(rf_volume* vol, const DevFrame& f, const double* T, unsigned far_raw, uint16_t* out,
                                cudaStream_t st);
 rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st);
+// residual seeds + erosion, and dilation, of several streams in one launch
+// each (grid y = stream; max_npix bounds every stream's pixel count; the
+// guard counts and flood-fill words are reset by the caller)
+MaskDesc make_mask_desc(rf_volume* vol, const DevFrame& f, const double* T, uint8_t* mask_out);
+rf_status launch_mask_pre_batch(rf_volume* vol, const MaskDesc* descs, int n, int max_npix, cudaStream_t st);
+rf_status launch_mask_post_batch(rf_volume* vol, const MaskDesc* descs, int n, int max_npix, cudaStream_t st);
 // profiling events (no-ops unless profiling is enabled); ids below
 enum ProfEvent { EV_FRAME0, EV_TRACK1_END, EV_MASK_END, EV_TRACK2_END, EV_INTEG0, EV_KERNEL0, EV_KERNEL1, EV_FRAME1,
                  EV_COUNT };

@@ -55,10 +55,11 @@ __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevPar
   return __dmul_rn(V, V);
 }
 
+// Seeds of the 256 pixels of CTA `block` (blockDim.x = 256).
 template <int ST>
-__global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p, const double* __restrict__ T,
-                                               uint8_t* __restrict__ seeds, unsigned* guard_count) {
-  if (gated_off(f.gate, kModeTrack)) return;
+__device__ __forceinline__ void seeds_body(const DevVol& v, const DevFrame& f, const DevParams& p,
+                                           const double* __restrict__ T, uint8_t* __restrict__ seeds,
+                                           unsigned* guard_count, int block) {
   // pose and threshold converted once per CTA (conversions use the FP64 pipe)
   __shared__ float sR[12];
   __shared__ double s_t64;
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p
   }
   if (threadIdx.x == 12) s_t64 = __dmul_rn(__dmul_rn(p.gamma_d, p.tau_d), p.tau_d);
   __syncthreads();
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = block * blockDim.x + threadIdx.x;
   if (idx >= f.H * f.W) return;
   const int u = idx % f.W, vv = idx / f.W;
   const unsigned raw = __ldg(f.depth + idx);
@@ -133,11 +134,23 @@ __global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p
   seeds[idx] = seed;
 }
 
-__global__ void __launch_bounds__(256) k_erode(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ mr,
-                                               const int* gate) {
-  if (gated_off(gate, kModeTrack)) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= H * W) return;
+template <int ST>
+__global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p, const double* __restrict__ T,
+                                               uint8_t* __restrict__ seeds, unsigned* guard_count) {
+  if (gated_off(f.gate, kModeTrack)) return;
+  seeds_body<ST>(v, f, p, T, seeds, guard_count, blockIdx.x);
+}
+
+// grid (x, n streams): the seeds of every tracked stream of a batch.
+template <int ST>
+__global__ void __launch_bounds__(256) k_seeds_batch(const MaskDesc* __restrict__ descs) {
+  const MaskDesc& d = descs[blockIdx.y];
+  if (gated_off(d.f.gate, kModeTrack) || (int)(blockIdx.x * blockDim.x) >= d.f.H * d.f.W) return;
+  seeds_body<ST>(d.v, d.f, d.p, d.T, d.seeds, d.guard, blockIdx.x);
+}
+
+__device__ __forceinline__ void erode_px(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ mr,
+                                         int idx) {
   const int u = idx % W, v = idx / W;
   uint8_t all = 1;
   if (u == 0 || v == 0 || u == W - 1 || v == H - 1) {
@@ -151,11 +164,15 @@ __global__ void __launch_bounds__(256) k_erode(const uint8_t* __restrict__ in, i
   mr[idx] = all;
 }
 
-__global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ out,
-                                                const int* gate) {
+__global__ void __launch_bounds__(256) k_erode(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ mr,
+                                               const int* gate) {
   if (gated_off(gate, kModeTrack)) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= H * W) return;
+  if (idx < H * W) erode_px(in, H, W, mr, idx);
+}
+
+__device__ __forceinline__ void dilate_px(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ out,
+                                          int idx) {
   const int u = idx % W, v = idx / W;
   uint8_t any = 0;
   for (int dv = -1; dv <= 1; ++dv) {
@@ -168,6 +185,28 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ in, 
     }
   }
   out[idx] = any;
+}
+
+__global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ out,
+                                                const int* gate) {
+  if (gated_off(gate, kModeTrack)) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < H * W) dilate_px(in, H, W, out, idx);
+}
+
+// grid (x, n streams): erosion and dilation of every tracked stream of a batch.
+__global__ void __launch_bounds__(256) k_erode_batch(const MaskDesc* __restrict__ descs) {
+  const MaskDesc& d = descs[blockIdx.y];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gated_off(d.f.gate, kModeTrack) || idx >= d.f.H * d.f.W) return;
+  erode_px(d.seeds, d.f.H, d.f.W, d.md, idx);
+}
+
+__global__ void __launch_bounds__(256) k_dilate_batch(const MaskDesc* __restrict__ descs) {
+  const MaskDesc& d = descs[blockIdx.y];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gated_off(d.f.gate, kModeTrack) || idx >= d.f.H * d.f.W) return;
+  dilate_px(d.md, d.f.H, d.f.W, d.mask_out, idx);
 }
 
 constexpr int kFFW = 32, kFFH = 16;  // flood-fill tile (one thread per pixel)
@@ -282,6 +321,34 @@ rf_status launch_mask_ff(rf_volume* vol, const DevFrame& f, cudaStream_t st) {
                     cudaLaunchKernelEx(&cfg, k_floodfill, vol->d_md, f.depth, f.H, f.W, vol->dp.theta_ppm, vol->d_ff,
                                        vol->p.max_ff_sweeps, vol->d_status, f.gate),
                     "flood-fill launch");
+}
+
+MaskDesc make_mask_desc(rf_volume* vol, const DevFrame& f, const double* T, uint8_t* mask_out) {
+  MaskDesc d;
+  d.v = vol->dv;
+  d.f = f;
+  d.p = vol->dp;
+  d.T = T;
+  d.seeds = vol->d_seeds;
+  d.guard = vol->d_guard;
+  d.md = vol->d_md;
+  d.mask_out = mask_out;
+  return d;
+}
+
+rf_status launch_mask_pre_batch(rf_volume* vol, const MaskDesc* descs, int n, int max_npix, cudaStream_t st) {
+  const dim3 grid((unsigned)((max_npix + 255) / 256), (unsigned)n);
+  if (vol->p.storage == RF_STORAGE_FP16)
+    k_seeds_batch<RF_STORAGE_FP16><<<grid, 256, 0, st>>>(descs);
+  else
+    k_seeds_batch<RF_STORAGE_FP32><<<grid, 256, 0, st>>>(descs);
+  k_erode_batch<<<grid, 256, 0, st>>>(descs);
+  return check_cuda(vol, cudaGetLastError(), "batched mask launch");
+}
+
+rf_status launch_mask_post_batch(rf_volume* vol, const MaskDesc* descs, int n, int max_npix, cudaStream_t st) {
+  k_dilate_batch<<<dim3((unsigned)((max_npix + 255) / 256), (unsigned)n), 256, 0, st>>>(descs);
+  return check_cuda(vol, cudaGetLastError(), "batched mask launch");
 }
 
 rf_status launch_mask_post(rf_volume* vol, const DevFrame& f, uint8_t* mask_out, cudaStream_t st) {
