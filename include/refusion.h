@@ -247,10 +247,13 @@ rf_status rf_process_frame_host(rf_volume* vol, int height, int width, const dou
                                 double T_out_host[16], uint8_t* mask_host, void* stream);
 
 /* Batches: one frame for each of n volumes (independent camera streams, any
- * mix of resolutions and voxel sizes) per call.  The two registrations of all
- * streams run as one cooperative launch each, with one group of CTAs per
- * tracked stream sized by its pixel count (the groups never wait on each
- * other); the masks and integrations of the streams run concurrently.  A
+ * mix of resolutions and voxel sizes) per call.  Each of the two
+ * registrations runs as cooperative launches over groups of at most
+ * batch_group tracked streams (rf_launch_config), with one set of CTAs per
+ * stream sized by its pixel count (the sets never wait on each other); the
+ * residual seeds, erosions and dilations of all streams run as one launch
+ * each, the flood fills as one cooperative launch per group, and the
+ * integrations of the streams concurrently.  A
  * stream's result is bit-identical to processing it alone with
  * rf_process_frame (partial sums are taken over fixed pixel chunks, not per
  * CTA).

@@ -4,8 +4,8 @@ Every admitted stream owns a slot: a device-resident volume (hash table,
 voxel pool, staging) plus its pose, kept on the device between frames.
 Frames arrive on each stream's own clock.  Each iteration of the loop runs
 ONE rf_batch_process over all slots: streams with an arrived frame process it
-(both registrations of all of them in one cooperative launch, masks and
-integrations concurrently); the other slots sit the call out, which costs
+(each registration as cooperative launches over groups of streams, the mask
+stages as one launch each over all streams, integrations concurrently); the other slots sit the call out, which costs
 them nothing but an empty pass and keeps the captured graph the same, so
 frames that arrive while a batch is on the GPU simply join the next one.
 
