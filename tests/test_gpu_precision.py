@@ -241,3 +241,59 @@ def test_fp16_process_frame_follows_fp32(R):
     worst_r = max(P.pose_diff(a, b)[1] for a, b in zip(out[0], out[1]))
     print(f"FP16 vs FP32 storage, free-running: {worst:.2e} m, {worst_r:.2e} rad")
     assert worst < 2e-3 and worst_r < math.radians(0.1)
+
+
+def test_fp16_precision_form_full_size(R, O):
+    """The precision form at its full sizes: 1280x720 (fx = fy = 1050), 0.5 cm
+    voxels, tau = 5 cm, 2^22 buckets, FP16 storage.  (1) One frame integrated
+    at ground truth on both sides: exact blocks, weights and colours, the SDF
+    within one update's rounding bound.  (2) On the oracle's FP16-rounded
+    snapshot: the mask of the next frame with a nearer fronto-parallel
+    rectangle pasted in (an object the model does not hold), bit-exact and
+    non-trivial; and registration from the previous frame's pose and from a
+    perturbed one within 1e-4 m and 1e-4 rad of the oracle."""
+    tau, voxel = 0.05, 0.005
+    seq = make_sequence("precision", 0, n_frames=2)
+    cam = seq.camera
+    assert (cam.width, cam.height, cam.fx) == (1280, 720, 1050.0)
+    d0, rgb0, T0, _ = seq.frame(0)
+    d1, rgb1, T1, _ = seq.frame(1)
+    orc = O.OracleVolume(voxel_size=voxel, trunc=tau)
+    orc.integrate(P.orc_frame(O, d0, rgb0, cam), T0)
+    os_ = orc.export()
+    vol = fp16_volume(R, cam, voxel, trunc=tau, n_buckets=1 << 22, max_blocks=200000)
+    vol.integrate(P.dev_frame(R, vol, d0, rgb0, cam), T0)
+    vol.sync()
+    gs = vol.export()
+    gk = {tuple(c): k for k, c in enumerate(gs["coords"])}
+    assert set(gk) == {tuple(c) for c in os_["coords"]} and len(gk) > 10000
+    order = np.array([gk[tuple(c)] for c in os_["coords"]], dtype=np.int64)
+    for key in ("W", "wc", "rgb"):
+        np.testing.assert_array_equal(gs[key][order], os_[key])
+    obs = os_["W"] > 0
+    err = np.abs(gs["F"][order].astype(np.float64) - os_["F"])[obs]
+    assert err.max() <= (HALF_UNIT + 1e-5) * tau, err.max() / tau
+    vol.close()
+
+    snap = fp16_snapshot(P.to_f32_snapshot(os_), tau=tau)
+    o2 = O.OracleVolume(voxel_size=voxel, trunc=tau)
+    o2.import_(snap)
+    v2 = fp16_volume(R, cam, voxel, trunc=tau, n_buckets=1 << 22, max_blocks=200000)
+    v2.import_(snap)
+    d_obj = d1.copy()
+    d_obj[240:480, 400:800] = 600  # a fronto-parallel rectangle at 0.6 m, nearer than the room
+    m_gpu = v2.compute_mask(P.dev_frame(R, v2, d_obj, rgb1, cam), T1)
+    v2.sync()
+    m_orc = o2.compute_mask(P.orc_frame(O, d_obj, rgb1, cam), T1)
+    np.testing.assert_array_equal(m_gpu.cpu().numpy(), m_orc)
+    assert m_orc[240:480, 400:800].all() and 0.1 < m_orc.mean() < 0.11  # the rectangle and its dilation
+    fr = P.dev_frame(R, v2, d1, rgb1, cam)
+    of = P.orc_frame(O, d1, rgb1, cam)
+    # from the previous frame's pose (a 7.7 mm / 0.78 deg step) and from a small perturbation
+    for Ts in (T0, O.se3_exp(np.array([0.004, -0.003, 0.002, 0.003, -0.002, 0.004])) @ T1):
+        Tgpu, _ = v2.track(fr, Ts)
+        v2.sync()
+        Torc, _ = o2.track(of, Ts)
+        dt, dr = P.pose_diff(Tgpu.cpu().numpy(), Torc)
+        assert dt < P.POSE_TOL and dr < P.POSE_TOL, (dt, dr)
+    v2.close()
