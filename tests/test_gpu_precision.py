@@ -25,7 +25,7 @@ import numpy as np
 import pytest
 
 from synth import make_sequence
-from synth.scenes import CAM_QVGA, CAM_TINY
+from synth.scenes import CAM_HD, CAM_QVGA, CAM_TINY, CAM_VGA
 
 from . import test_gpu_parity as P
 from ._scenes import ROOM, corner_pose, render_frame
@@ -170,17 +170,18 @@ def test_fp16_tracking_vs_oracle(R, O):
     print(f"FP16 storage: pose vs oracle {worst[0]:.2e} m, {worst[1]:.2e} rad")
 
 
-def test_fp16_batch_is_bit_identical_to_single_streams(R):
-    specs = [("tiny", 0, None, 0.02), ("dynamic", 1, CAM_QVGA, 0.03)]
-    seqs = [make_sequence(c, sd, n_frames=4, camera=cam) for c, sd, cam, _ in specs]
+def _batch_vs_single(R, specs, n_frames, n_buckets, max_blocks):
+    """Each stream's poses, masks and final volume from one FP16 batch, and
+    from rf_process_frame on the stream alone, must be identical."""
+    seqs = [make_sequence(c, sd, n_frames=n_frames, camera=cam) for c, sd, cam, _ in specs]
     outs = {}
     for mode in ("single", "batch"):
-        vols = [fp16_volume(R, s.camera, vx, n_buckets=1 << 16, max_blocks=100000)
+        vols = [fp16_volume(R, s.camera, vx, n_buckets=n_buckets, max_blocks=max_blocks)
                 for s, (_, _, _, vx) in zip(seqs, specs)]
         batch = R.Batch(vols) if mode == "batch" else None
         T = [None] * len(seqs)
         poses, masks = [], []
-        for i in range(4):
+        for i in range(n_frames):
             frames, tin, tout, mk = [], [], [], []
             for k, s in enumerate(seqs):
                 d, rgb, Tgt, _ = s.frame(i)
@@ -210,6 +211,20 @@ def test_fp16_batch_is_bit_identical_to_single_streams(R):
     for sa, sb in zip(outs["single"][2], outs["batch"][2]):
         for key in ("coords", "F", "W", "rgb", "wc"):
             np.testing.assert_array_equal(sa[key], sb[key])
+    return outs
+
+
+def test_fp16_batch_is_bit_identical_to_single_streams(R):
+    _batch_vs_single(R, [("tiny", 0, None, 0.02), ("dynamic", 1, CAM_QVGA, 0.03)], 4, 1 << 16, 100000)
+
+
+def test_fp16_batch_full_size_serving_resolutions(R):
+    """The serving workload's three resolutions in one FP16 batch at full
+    size: 1280x720 at 2 cm, 640x480 with movers at 1 cm, 320x240 with movers
+    at 3 cm; three frames each, identical to each stream alone."""
+    outs = _batch_vs_single(R, [("precision", 0, CAM_HD, 0.02), ("dynamic", 1, CAM_VGA, 0.01),
+                                ("dynamic", 2, CAM_QVGA, 0.03)], 3, 1 << 18, 200000)
+    assert all(len(s["coords"]) > 100 for s in outs["batch"][2])  # ~770, ~7900, ~270 blocks
 
 
 def test_fp16_and_fp32_volumes_do_not_share_a_batch(R):
