@@ -278,6 +278,7 @@ rf_status rf_batch_create(rf_volume* const* vols, int n, rf_batch** out);
 rf_status rf_batch_destroy(rf_batch* batch);
 rf_status rf_batch_process(rf_batch* batch, const rf_frame* frames, const double* const* T_init_dev,
                            double* const* T_out_dev, uint8_t* const* mask_dev, void* stream);
+/* Message of the last failing batch call ("" for NULL). */
 const char* rf_batch_last_error(rf_batch* batch);
 
 /* Zero-crossing surface of the TSDF (the mesh of Sec. I) by marching
@@ -302,6 +303,10 @@ rf_status rf_volume_export(rf_volume* vol, int64_t cap_blocks, int32_t* coords, 
 rf_status rf_volume_import(rf_volume* vol, int64_t n_blocks, const int32_t* coords, const float* F,
                            const uint8_t* W, const uint8_t* rgb, const uint8_t* wc);
 
+/* Block count, capacity, frames processed, hash load factor and device bytes
+ * of the volume: host-side bookkeeping plus one synchronous read of the
+ * device block counter (synchronise the volume's stream first to count its
+ * last frame). */
 rf_status rf_volume_stats(rf_volume* vol, rf_stats* out);
 
 /* Launch shapes of the kernels whose best grid depends on the device and the
