@@ -212,9 +212,13 @@ class ClockSampler:
 
 
 FLOPS_PER_SAMPLE = 320  # FP32 flops of one sampled pixel in one cost evaluation (depth + colour terms)
-# DRAM bytes (read + write) of one k_integrate launch on this workload, from the ncu capture summarised in
-# profiles/k_integrate_static_640x480.md (to be reset to None when the kernel changes)
-INTEGRATE_DRAM_BYTES = 37.697792e6 + 86.528e3
+# DRAM bytes (read + write) per launch on this workload from ncu captures (None once the kernel has changed
+# since its capture).  k_register: profiles/k_register_static_640x480.md, current code.  k_integrate:
+# profiles/k_integrate_static_640x480.md was captured before the per-voxel loop moved into a device function
+# (same loads and stores, same 96 registers), so its figure is context only.
+REGISTER_DRAM_BYTES = 6.876160e6 + 50.432e3
+INTEGRATE_DRAM_BYTES = None
+INTEGRATE_DRAM_BYTES_EARLIER = 37.697792e6 + 86.528e3
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -618,14 +622,17 @@ def main():
             "stages_ms": stage,
             "roofline": {"bound": "alu", "kernel": "k_register (one registration: 3 levels, all LM evaluations)",
                          "achieved": reg_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": reg_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": reg_tflops / FP32_PEAK_TFLOPS, "traffic": REGISTER_DRAM_BYTES,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
                          "flops_per_launch": statistics.mean(reg_flops), "launch_ms": statistics.mean(reg_ms),
                          "note": "latency-bound: dependent LM chain with a grid barrier per evaluation"},
             "roofline_integrate": {"bound": "hbm", "kernel": "k_integrate (per-voxel TSDF/colour update)",
                                    "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                    "traffic": INTEGRATE_DRAM_BYTES,
-                                   "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch", "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
+                                   "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch; "
+                                                     f"{INTEGRATE_DRAM_BYTES_EARLIER:.4g} B before a source refactor",
+                                   "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
                                    "bytes_per_launch": statistics.mean(bytes_per),
                                    "launch_ms": statistics.mean(kern_ms)},
             "frame_hbm": {"achieved": frame_gbs, "peak": peak, "unit": "GB/s", "frac": frame_gbs / peak},
