@@ -10,6 +10,7 @@
 #include <cstring>
 #include <vector>
 
+#include "rf_cta_map.hpp"
 #include "rf_half.hpp"
 #include "rf_volume.hpp"
 
@@ -468,55 +469,8 @@ void join_aux(rf_batch* b, cudaStream_t cs) {
   }
 }
 
-// CTA groups of the batched registration: streams of weight 0 get none, the
-// others at least one and the rest in proportion to their weight (pixel
-// count), largest remainders first.
-std::vector<int> split_ctas(const std::vector<double>& weight, int total) {
-  const int n = (int)weight.size();
-  std::vector<int> cnt(n, 0);
-  double wsum = 0.0;
-  int active = 0;
-  for (int i = 0; i < n; ++i)
-    if (weight[i] > 0.0) {
-      cnt[i] = 1;
-      wsum += weight[i];
-      ++active;
-    }
-  if (active == 0) return cnt;
-  const int spare = total - active;
-  std::vector<std::pair<double, int>> rem;
-  int given = 0;
-  for (int i = 0; i < n; ++i) {
-    if (weight[i] <= 0.0) continue;
-    const double share = spare * weight[i] / wsum;
-    const int whole = (int)share;
-    cnt[i] += whole;
-    given += whole;
-    rem.push_back({share - whole, i});
-  }
-  std::sort(rem.begin(), rem.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
-    return x.first != y.first ? x.first > y.first : x.second < y.second;
-  });
-  for (int k = 0; k < spare - given && k < (int)rem.size(); ++k) cnt[rem[k].second]++;
-  return cnt;
-}
-
 size_t table_bytes(int n, int total_ctas, int ff_ctas, int ngroups) {
   return sizeof(BatchStage) * n + sizeof(int) * (size_t)ngroups * ((total_ctas + n + 1) + (ff_ctas + n + 1));
-}
-
-// CTA map of one launch: the CTAs split among the streams of weight > 0.
-void fill_cta_map(const std::vector<double>& w, int total, int* cta_stream) {
-  const int n = (int)w.size();
-  int* group_first = cta_stream + total;
-  const std::vector<int> cnt = split_ctas(w, total);
-  int c = 0;
-  for (int i = 0; i < n; ++i) {
-    group_first[i] = c;
-    for (int k = 0; k < cnt[i]; ++k) cta_stream[c++] = i;
-  }
-  group_first[n] = c;
-  for (; c < total; ++c) cta_stream[c] = -1;
 }
 
 // Captures the batch graph for one shape.  Every stream gets the full path;
@@ -1125,9 +1079,11 @@ rf_status rf_batch_create(rf_volume* const* vols, int n, rf_batch** out) {
     if (vols[i]->p.storage != vols[0]->p.storage)
       return set_error(nullptr, RF_ERR_INVALID_ARG, "volumes of one batch must share the storage mode");
   }
-  if (n > vols[0]->reg_grid)
+  // every tracked stream needs at least one CTA of a registration and of a flood-fill launch
+  const int max_streams = std::min(vols[0]->reg_grid, vols[0]->ff_grid);
+  if (n > max_streams)
     return set_error(nullptr, RF_ERR_INVALID_ARG, "rf_batch_create: at most %d streams per batch on this device",
-                     vols[0]->reg_grid);
+                     max_streams);
   rf_batch* b = new rf_batch();
   b->vols.assign(vols, vols + n);
   b->device = dev;
