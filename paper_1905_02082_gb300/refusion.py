@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librefusion.so")
 
 RF_OK = 0
+RF_ERR_INVALID_ARG = 1
 STATUS_NAMES = {0: "RF_OK", 1: "RF_ERR_INVALID_ARG", 2: "RF_ERR_CUDA", 3: "RF_ERR_HASH_FULL", 4: "RF_ERR_POOL_FULL",
                 5: "RF_ERR_NOT_CONVERGED", 6: "RF_ERR_BUFFER_TOO_SMALL", 7: "RF_ERR_OUT_OF_RANGE",
                 8: "RF_ERR_CAPACITY"}
@@ -465,6 +466,10 @@ class Batch:
         """frames: list of rf_frame; T_inits/T_outs: device float64 [4,4] tensors;
         masks: optional list of device uint8 [H,W] tensors (or None entries)."""
         n = len(self.volumes)
+        if not getattr(self, "h", None) or any(not getattr(v, "h", None) for v in self.volumes):
+            raise RFError(RF_ERR_INVALID_ARG, "batch or one of its volumes is closed")
+        if not (len(frames) == len(T_inits) == len(T_outs) == n) or (masks is not None and len(masks) != n):
+            raise RFError(RF_ERR_INVALID_ARG, f"a batch of {n} volumes takes {n} frames, poses and masks")
         fr = (rf_frame * n)(*frames)
         tin = (C.c_void_p * n)(*[t.data_ptr() for t in T_inits])
         tout = (C.c_void_p * n)(*[t.data_ptr() for t in T_outs])

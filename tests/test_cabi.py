@@ -111,3 +111,18 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(R, "_lib", None)
     with pytest.raises(ImportError):
         R.load(str(tmp_path / "librefusion.so"))
+
+
+def test_batch_rejects_closed_volumes_and_mismatched_lists():
+    """Checked in the binding before anything reaches the library."""
+    import types
+    import paper_1905_02082_gb300.refusion as R
+    b = R.Batch.__new__(R.Batch)
+    b.volumes = [types.SimpleNamespace(h=1), types.SimpleNamespace(h=None)]
+    b.h = 1
+    with pytest.raises(R.RFError):
+        b.process([None, None], [None, None], [None, None])
+    b.volumes[1].h = 2
+    with pytest.raises(R.RFError):
+        b.process([None], [None, None], [None, None])
+    b.h = None  # nothing to release
