@@ -134,7 +134,8 @@ def _ptr(t) -> Optional[int]:
     if hasattr(t, "data_ptr"):
         return t.data_ptr()
     if isinstance(t, np.ndarray):
-        assert t.flags["C_CONTIGUOUS"]
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the library must be C-contiguous")
         return t.ctypes.data
     return int(t)
 
@@ -181,9 +182,12 @@ def make_frame(depth, rgb, fx, fy, cx, cy) -> rf_frame:
     """rf_frame over tensors depth [H,W] uint16 and rgb [H,W,3] uint8, on the
     device or in page-locked host memory."""
     H, W = int(depth.shape[0]), int(depth.shape[1])
-    assert tuple(rgb.shape) == (H, W, 3)
-    assert depth.is_contiguous() and rgb.is_contiguous()
-    assert (depth.is_cuda or depth.is_pinned()) and (rgb.is_cuda or rgb.is_pinned())
+    if depth.dim() != 2 or depth.element_size() != 2 or tuple(rgb.shape) != (H, W, 3) or rgb.element_size() != 1:
+        raise ValueError("depth must be [H, W] 16-bit and rgb [H, W, 3] 8-bit")
+    if not (depth.is_contiguous() and rgb.is_contiguous()):
+        raise ValueError("depth and rgb must be contiguous")
+    if not ((depth.is_cuda or depth.is_pinned()) and (rgb.is_cuda or rgb.is_pinned())):
+        raise ValueError("depth and rgb must be device or page-locked host tensors")
     return rf_frame(H, W, float(fx), float(fy), float(cx), float(cy), depth.data_ptr(), rgb.data_ptr())
 
 
@@ -222,6 +226,15 @@ def rf_process_frame(h, frame: rf_frame, T_init, T_out, mask_out=None, info=None
 def rf_process_frame_host(h, depth: np.ndarray, rgb: np.ndarray, intr, T_init: np.ndarray, T_out: np.ndarray,
                           mask: Optional[np.ndarray] = None, stream=None):
     intr = np.ascontiguousarray(intr, dtype=np.float64)
+    H, W = depth.shape[0], depth.shape[1]
+    if depth.dtype != np.uint16 or depth.ndim != 2 or rgb.dtype != np.uint8 or rgb.shape != (H, W, 3):
+        raise ValueError("depth must be uint16 [H, W] and rgb uint8 [H, W, 3]")
+    if T_init.dtype != np.float64 or T_init.size != 16 or T_out.dtype != np.float64 or T_out.size != 16:
+        raise ValueError("poses must be float64 4x4")
+    if mask is not None and (mask.dtype != np.uint8 or mask.shape != (H, W)):
+        raise ValueError("mask must be uint8 [H, W]")
+    if intr.size != 4:
+        raise ValueError("intrinsics are fx, fy, cx, cy")
     _check(load().rf_process_frame_host(h, depth.shape[0], depth.shape[1], _ptr(intr), _ptr(depth), _ptr(rgb),
                                         _ptr(T_init), _ptr(T_out), _ptr(mask), _stream(stream)), h)
 

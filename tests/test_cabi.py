@@ -126,3 +126,20 @@ def test_batch_rejects_closed_volumes_and_mismatched_lists():
     with pytest.raises(R.RFError):
         b.process([None], [None, None], [None, None])
     b.h = None  # nothing to release
+
+
+def test_binding_checks_image_arguments():
+    import numpy as np
+    import torch
+    import paper_1905_02082_gb300.refusion as R
+    d = torch.zeros(4, 6, dtype=torch.int16)
+    with pytest.raises(ValueError):  # pageable host memory
+        R.make_frame(d, torch.zeros(4, 6, 3, dtype=torch.uint8), 1.0, 1.0, 2.0, 2.0)
+    with pytest.raises(ValueError):  # wrong colour shape
+        R.make_frame(d, torch.zeros(4, 6, dtype=torch.uint8), 1.0, 1.0, 2.0, 2.0)
+    T = np.eye(4)
+    with pytest.raises(ValueError):  # float depth
+        R.rf_process_frame_host(None, np.zeros((4, 6)), np.zeros((4, 6, 3), np.uint8), [1, 1, 2, 2], T, T.copy())
+    with pytest.raises(ValueError):  # float32 pose
+        R.rf_process_frame_host(None, np.zeros((4, 6), np.uint16), np.zeros((4, 6, 3), np.uint8), [1, 1, 2, 2],
+                                T.astype(np.float32), T.copy())
