@@ -212,10 +212,10 @@ class ClockSampler:
 
 
 FLOPS_PER_SAMPLE = 320  # FP32 flops of one sampled pixel in one cost evaluation (depth + colour terms)
-# DRAM bytes (read + write) per launch on this workload from ncu captures (None once the kernel has changed
-# since its capture).  k_register: profiles/k_register_static_640x480.md, current code.  k_integrate:
-# profiles/k_integrate_static_640x480.md was captured before the per-voxel loop moved into a device function
-# (same loads and stores, same 96 registers), so its figure is context only.
+# DRAM bytes (read + write) per launch on this workload from one ncu capture each (None once the kernel has
+# changed since its capture).  k_register: captured on the current code.  k_integrate: captured before its
+# per-voxel loop moved into a device function (same loads and stores, same 96 registers), so that figure is
+# context only.
 REGISTER_DRAM_BYTES = 6.876160e6 + 50.432e3
 INTEGRATE_DRAM_BYTES = None
 INTEGRATE_DRAM_BYTES_EARLIER = 37.697792e6 + 86.528e3
