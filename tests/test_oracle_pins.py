@@ -764,3 +764,117 @@ def test_virtual_depth_of_a_sphere_matches_the_ray_intersection(oracle_mod):
     tan = np.sqrt(np.clip(1.0 - facing[sel] ** 2, 0.0, None)) / facing[sel]
     bound = 0.5 + 1000.0 * 0.5 * z[sel] / cam.fx * tan + 0.5  # + rounding of the result
     assert np.all(err <= bound), float((err - bound).max())
+
+
+# ---------------------------------------------------------------------------
+# closed-form pins of the mask residual, the colour average and tracking
+# ---------------------------------------------------------------------------
+
+# A camera whose pixels back-project onto the voxel lattice: with fx = fy =
+# 128, principal point (80, 60), voxel 8 mm and a depth of 1.024 m, pixel
+# (u, v) lands on lattice point (u - 80, v - 60, 128) exactly.
+LATTICE_CAM = Camera(160, 120, 128.0, 128.0, 80.0, 60.0)
+LATTICE_VOXEL = 0.008
+LATTICE_DEPTH_MM = 1024
+
+
+def _lattice_texture(kx, ky):
+    """Integer grey level of lattice column (kx, ky): a smooth texture with
+    gradients along x and y (values 28..228)."""
+    return np.rint(128.0 + 50.0 * np.sin(2 * np.pi * kx / 37.0) + 50.0 * np.sin(2 * np.pi * ky / 29.0 + 1.0))
+
+
+def _lattice_plane_snapshot(z_margin=0.2):
+    """Model of the plane z = 1.024 m seen by LATTICE_CAM at the identity pose:
+    F(p) = 1.024 - p_z (affine, positive in front), voxel colour the grey
+    texture of its (kx, ky) column."""
+    v = LATTICE_VOXEL
+    zc = LATTICE_DEPTH_MM / 1000.0
+    reach = (LATTICE_CAM.width / 2 + 2) / LATTICE_CAM.fx * (zc + z_margin)
+    bx = np.arange(int(np.floor(-reach / (8 * v))) - 1, int(np.floor(reach / (8 * v))) + 2)
+    by = np.arange(int(np.floor(-reach * 0.75 / (8 * v))) - 1, int(np.floor(reach * 0.75 / (8 * v))) + 2)
+    bz = np.arange(int(np.floor((zc - z_margin) / (8 * v))), int(np.floor((zc + z_margin) / (8 * v))) + 1)
+    zz, yy, xx = np.meshgrid(bz, by, bx, indexing="ij")
+    coords = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
+    return _snapshot_from_field(coords, lambda p: zc - p[..., 2], v,
+                                colour_fn=lambda k: _lattice_texture(k[..., 0], k[..., 1]))
+
+
+def _lattice_frame(depth_mm):
+    cam = LATTICE_CAM
+    vs, us = np.mgrid[0:cam.height, 0:cam.width]
+    depth = np.full((cam.height, cam.width), depth_mm, np.uint16)
+    g = _lattice_texture(us - 80, vs - 60).astype(np.uint8)
+    return depth, np.repeat(g[..., None], 3, axis=2)
+
+
+def test_mask_residual_is_the_squared_sdf_of_an_offset_plane(oracle_mod):
+    """Eq. 2's underbraced term r_i = V_SDF(T x_i)^2 against a closed form: a
+    frame of the plane moved by delta along the view gives V_SDF = -delta at
+    every pixel (the model is affine, so trilinear lookup is exact), hence
+    r_i = delta^2, and tau^2 once |delta| > tau (the TSDF is truncated at tau,
+    Sec. III-A).  Eq. 5 seeds r_i > gamma tau^2 = 0.005 at gamma = 0.5,
+    tau = 0.1: the decision flips between |delta| = 60 mm and 80 mm.  Seeding
+    on |V_SDF| instead of its square would seed at 60 mm already."""
+    O = oracle_mod
+    vol = O.OracleVolume(voxel_size=LATTICE_VOXEL, trunc=0.1, gamma=0.5)
+    vol.import_(_lattice_plane_snapshot())
+    for delta_mm, seeded in ((-150, True), (-80, True), (-60, False), (0, False), (60, False), (80, True),
+                             (150, True)):
+        depth, rgb = _lattice_frame(LATTICE_DEPTH_MM + delta_mm)
+        r, seeds = vol.residuals(_frame(O, depth, rgb, LATTICE_CAM), np.eye(4))
+        delta = delta_mm / 1000.0
+        expect = min(delta * delta, 0.1 * 0.1)
+        assert np.all(r >= 0.0)  # every pixel has a valid model lookup
+        np.testing.assert_allclose(r, expect, rtol=0, atol=1e-12)
+        assert seeds.all() if seeded else not seeds.any(), delta_mm
+
+
+def test_colour_running_average_rounds_half_up(oracle_mod):
+    """Colour running average (Sec. III-A; reading: RGB8 stored rounded half
+    up at every update, own weight Wc), hand-computed per channel:
+      (100, 50, 7) then (101, 53, 8): 100.5 -> 101, 51.5 -> 52, 7.5 -> 8
+      (truncation would give 100, 51, 7; round-half-even 100, 52, 8);
+      (100, 50, 7) twice then (101, 52, 9): 301/3 -> 100, 152/3 -> 51, 23/3 -> 8."""
+    O = oracle_mod
+    cam, voxel, tau = CAM_TINY, 0.02, 0.1
+    for colours, expect in ((((100, 50, 7), (101, 53, 8)), (101, 52, 8)),
+                            (((100, 50, 7), (100, 50, 7), (101, 52, 9)), (100, 51, 8))):
+        vol = O.OracleVolume(voxel_size=voxel, trunc=tau)
+        for c in colours:
+            depth, rgb = fronto_plane_frame(cam, 1503, c)
+            vol.integrate(_frame(O, depth, rgb, cam), np.eye(4))
+        got = _voxels_of(vol.export(), voxel_filter=lambda W: W > 0)
+        band = [v for v in got.values() if v[3] > 0]
+        assert len(band) > 1000
+        for F, W, col, wc in band:
+            assert col == expect and wc == len(colours), (col, expect, wc)
+
+
+def test_tracking_recovers_an_exact_minimiser(oracle_mod):
+    """A scene where the ground truth is an exact minimiser of Eq. 4: the
+    plane z = 1.024 m (affine TSDF model) with a grey texture on the voxel
+    lattice, seen by a camera whose pixels back-project onto lattice points,
+    so every depth and colour residual is zero at the true pose (the identity)
+    and the plane's normal plus the texture's two gradient directions observe
+    all six pose parameters.  From 2 cm / 1 degree perturbations LM must
+    return the ground truth to 1e-8 (convergence thresholds tightened so that
+    the levels run to machine precision)."""
+    O = oracle_mod
+    vol = O.OracleVolume(voxel_size=LATTICE_VOXEL, trunc=0.2, lm_iters=(10, 10, 30), lm_eps_trans=1e-13,
+                         lm_eps_rot=1e-13)
+    vol.import_(_lattice_plane_snapshot())
+    depth, rgb = _lattice_frame(LATTICE_DEPTH_MM)
+    f = _frame(O, depth, rgb, LATTICE_CAM)
+    H, g, E, N = vol.eval(f, np.eye(4), stride=1)
+    assert N == LATTICE_CAM.width * LATTICE_CAM.height and E < 1e-20  # zero residuals at the truth
+    assert np.linalg.eigvalsh(H).min() > 1e-6 * np.linalg.eigvalsh(H).max()  # no unobserved direction
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        xi = rng.normal(size=6)
+        xi[:3] *= 0.02 / np.linalg.norm(xi[:3])
+        xi[3:] *= math.radians(1.0) / np.linalg.norm(xi[3:])
+        T, info = vol.track(f, O.se3_exp(xi))
+        assert np.linalg.norm(T[:3, 3]) < 1e-8, T[:3, 3]
+        assert rot_err(T[:3, :3], np.eye(3)) < 1e-8
+        assert info.evals >= 4
