@@ -177,10 +177,10 @@ rf_status rf_track_frame(rf_volume* vol, const rf_frame* frame, const double* T_
 rf_status rf_compute_mask(rf_volume* vol, const rf_frame* frame, const double* T_dev, uint8_t* mask_dev,
                           void* stream);
 
-/* Same result as rf_compute_mask, for callers that cannot allocate device
- * memory when they need a mask: code running inside a CUDA stream capture in
- * global mode (where cudaMalloc is refused), or a host application that owns
- * all device memory through its own allocator or a fixed budget.  The paper has
+/* Same result as rf_compute_mask, for callers that cannot call cudaMalloc
+ * when they need a mask: an application whose own allocator or fixed memory
+ * budget owns all device memory, or a frame loop with a latency bound that
+ * cannot afford cudaMalloc's implicit device synchronisation.  The paper has
  * no counterpart; this is a property of the library only.
  *  - Allocates nothing: the per-call scratch (seed image, flood-fill working
  *    mask, barrier words, sweep flags) is one static device array of about
@@ -188,9 +188,10 @@ rf_status rf_compute_mask(rf_volume* vol, const rf_frame* frame, const double* T
  *  - Frames of at most 921,600 pixels (1280 x 720); larger frames return
  *    RF_ERR_INVALID_ARG with a message.  The flood fill is bounded by
  *    min(max_ff_sweeps, 4096) sweeps.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The current device must be the volume's device (RF_ERR_INVALID_ARG
+ *    otherwise).  The first call on a device looks up the array's device
+ *    address (cudaGetSymbolAddress) with that device current; make that first
+ *    call before any stream capture.
  *  - All calls share the one array: calls whose GPU work overlaps (other
  *    streams, other volumes, other host threads) race and corrupt each other's
  *    masks.  Serialise them, e.g. on one stream.

@@ -523,7 +523,7 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     prof[i] = b->vols[i]->profiling;
     b->vols[i]->profiling = false;  // per-volume profiling events are not used in batches
   }
-  cudaStream_t cs;
+  cudaStream_t cs = nullptr;
   e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   rf_status s = RF_OK;

@@ -447,11 +447,16 @@ extern "C" rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* fra
     return set_error(vol, RF_ERR_INVALID_ARG,
                      "rf_compute_mask_noalloc: frame of %d x %d pixels exceeds the static scratch limit of %d pixels",
                      frame->width, frame->height, kNoAllocMaxPixels);
+  // the kernels run on the current device and read the volume's memory: the
+  // two must be the same GPU (the scratch address is per device too)
   int device = 0;
   rf_status s = check_cuda(vol, cudaGetDevice(&device), "current device");
   if (s) return s;
+  if (device != vol->device)
+    return set_error(vol, RF_ERR_INVALID_ARG,
+                     "rf_compute_mask_noalloc: current device %d is not the volume's device %d", device, vol->device);
   cudaError_t e;
-  unsigned char* base = static_cast<unsigned char*>(mask_scratch_address(device, &e));
+  unsigned char* base = static_cast<unsigned char*>(mask_scratch_address(vol->device, &e));
   if (!base) return check_cuda(vol, e, "cudaGetSymbolAddress(mask scratch)");
   uint8_t* seeds = base;
   uint8_t* md = base + kNoAllocMaxPixels;

@@ -1,11 +1,13 @@
 """The allocation-free mask entry point (rf_compute_mask_noalloc).
 
-It serves callers that cannot allocate device memory at the time they need a
-mask (inside a CUDA stream capture in global mode, or under an application
-allocator that owns all device memory).  Its scratch is a static device array
-shared by all calls, so this checks that it reproduces rf_compute_mask
-exactly on two calls in a row with different inputs (the second call must not
-see the first call's leftovers) and that oversize frames are refused.
+It serves callers that cannot call cudaMalloc at the time they need a mask
+(an application whose own allocator or fixed budget owns all device memory,
+or a frame loop that cannot afford cudaMalloc's implicit synchronisation).
+Its scratch is a static device array shared by all calls, so this checks
+that it reproduces rf_compute_mask exactly on two calls in a row with
+different inputs (the second call must not see the first call's leftovers),
+that oversize frames are refused, and (with two GPUs) that a current device
+other than the volume's is refused.
 
 This file is collected last on purpose: it must pass alone in a fresh process
 and after every other test.
@@ -81,4 +83,23 @@ def test_noalloc_mask_rejects_frames_beyond_the_static_limit(R):
     with pytest.raises(R.RFError) as e:
         R.rf_compute_mask_noalloc(vol.h, fr, T, out)
     assert e.value.status == 1 and "static scratch limit" in str(e.value)
+    vol.close()
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2, reason="needs two GPUs")
+def test_noalloc_mask_refuses_a_current_device_other_than_the_volumes(R):
+    torch.cuda.set_device(0)
+    vol = R.Volume(n_buckets=1 << 10, max_blocks=1000, max_width=64, max_height=48, voxel_size=0.02)
+    d = torch.zeros(48, 64, dtype=torch.uint16, device="cuda:0")
+    rgb = torch.zeros(48, 64, 3, dtype=torch.uint8, device="cuda:0")
+    fr = vol.frame(d, rgb, R.Intrinsics(50.0, 50.0, 31.5, 23.5))
+    T = torch.eye(4, dtype=torch.float64, device="cuda:0")
+    out = torch.empty(48, 64, dtype=torch.uint8, device="cuda:0")
+    try:
+        torch.cuda.set_device(1)
+        with pytest.raises(R.RFError) as e:
+            R.rf_compute_mask_noalloc(vol.h, fr, T, out)
+        assert e.value.status == 1 and "volume's device" in str(e.value)
+    finally:
+        torch.cuda.set_device(0)
     vol.close()
