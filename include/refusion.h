@@ -330,6 +330,19 @@ typedef struct rf_launch_config {
 rf_status rf_get_launch_config(rf_volume* vol, rf_launch_config* out);
 rf_status rf_set_launch_config(rf_volume* vol, const rf_launch_config* cfg);
 
+/* Bounded waits (a property of the library; the paper has no counterpart).
+ * Every grid-wide barrier of the cooperative kernels (registration, flood
+ * fill) polls at most spin_limit times before it gives up: the kernel then
+ * records RF_ERR_NOT_CONVERGED in the status word (rf_sync_status) and
+ * returns, and the volume stays usable.  spin_limit 0 restores the default,
+ * 2^24 polls (about one second).  extra_arrivals is fault injection for
+ * tests: with extra_arrivals > 0 each barrier waits for that many arrivals
+ * beyond the CTAs launched, which never come, so every wait runs out and the
+ * error path is exercised; use 0 otherwise.  Synchronises the device and
+ * drops the volume's captured graphs; batches keep the limits in force when
+ * they first saw a frame shape. */
+rf_status rf_set_wait_limits(rf_volume* vol, int64_t spin_limit, int extra_arrivals);
+
 /* Enables (1) or disables (0) device timing of the whole-frame calls: CUDA
  * events recorded on the caller's stream (kept inside the captured graphs)
  * around each stage and around the per-voxel update kernel.  Work counters

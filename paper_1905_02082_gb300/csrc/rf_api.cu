@@ -1006,6 +1006,19 @@ rf_status rf_set_launch_config(rf_volume* vol, const rf_launch_config* cfg) {
   return RF_OK;
 }
 
+rf_status rf_set_wait_limits(rf_volume* vol, int64_t spin_limit, int extra_arrivals) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  if (spin_limit < 0 || spin_limit > ((int64_t)1 << 40) || extra_arrivals < 0 || extra_arrivals > 1024)
+    return set_error(vol, RF_ERR_INVALID_ARG, "spin_limit must be in 0..2^40 and extra_arrivals in 0..1024");
+  rf_status s = check_cuda(vol, cudaDeviceSynchronize(), "wait limits sync");
+  if (s) return s;
+  for (auto& g : vol->graphs) cudaGraphExecDestroy(g.exec);  // their kernels hold the old limits
+  vol->graphs.clear();
+  vol->wait_spins = spin_limit == 0 ? kDefaultSpinLimit : (long long)spin_limit;
+  vol->wait_extra = (unsigned)extra_arrivals;
+  return RF_OK;
+}
+
 rf_status rf_volume_stats(rf_volume* vol, rf_stats* out) {
   if (!vol || !out) return RF_ERR_INVALID_ARG;
   int nb = 0;

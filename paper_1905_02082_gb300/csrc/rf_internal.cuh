@@ -118,6 +118,8 @@ struct RegDesc {
   int max_chunks;
   unsigned* bar;
   unsigned* status;
+  long long spin_limit;  // bound of each grid-barrier wait (polls)
+  unsigned bar_extra;    // fault injection: arrivals each barrier waits for beyond the CTAs launched
   // per full-resolution pixel: the (block key << 22 | pool) its last sample
   // was found in, ~0 when none; a block's pool never changes until the
   // volume is reset or imported, which clear the cache.  nullptr: no cache
@@ -288,10 +290,16 @@ __device__ __forceinline__ bool pixel_valid(const DevParams& p, unsigned raw) {
   return raw != 0 && D >= p.dmin_um && D <= p.dmax_um;
 }
 
+// Default bound of a grid-barrier wait: 2^24 polls (after the first 4,096 each
+// followed by a 64 ns sleep), about one second.
+constexpr long long kDefaultSpinLimit = 1ll << 24;
+
 // Grid-wide barrier for cooperative launches (all CTAs co-resident).  The
-// spin is bounded: after ~1 s it records ST_BARRIER and returns false, and
-// callers then leave the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+// spin is bounded: after spin_limit polls it records ST_BARRIER and returns
+// false, and callers then leave the kernel.  extra > 0 (fault injection for
+// tests) makes the barrier wait for arrivals that never come.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status, long long spin_limit,
+                                             unsigned extra) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -300,14 +308,14 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
     __threadfence();
     const unsigned ticket = atomicAdd(bar, 1u);
     int ok = 1;
-    if (ticket == nblocks - 1) {
+    if (ticket == nblocks + extra - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       long long spins = 0;
       while (*vgen == gen) {
-        if (++spins > (1ll << 24)) {
+        if (++spins > spin_limit) {
           ok = 0;
           atomicOr(status, ST_BARRIER);
           break;
@@ -338,7 +346,8 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync_counter(unsigned* count, unsigned target, unsigned* status) {
+__device__ __forceinline__ bool grid_sync_counter(unsigned* count, unsigned target, unsigned* status,
+                                                  long long spin_limit) {
   __shared__ int s_ok2;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -346,7 +355,7 @@ __device__ __forceinline__ bool grid_sync_counter(unsigned* count, unsigned targ
     int ok = 1;
     long long spins = 0;
     while (ld_acquire_gpu(count) < target) {
-      if (++spins > (1ll << 24)) {
+      if (++spins > spin_limit) {
         ok = 0;
         atomicOr(status, ST_BARRIER);
         break;
@@ -403,6 +412,8 @@ struct FloodDesc {
   unsigned* ff;
   int max_sweeps;
   unsigned* status;
+  long long spin_limit;
+  unsigned bar_extra;
 };
 FloodDesc make_flood_desc(rf_volume* vol, const DevFrame& f);
 rf_status launch_floodfill_batch(rf_volume* vol, const FloodDesc* descs, const int* cta_stream, const int* first,

@@ -220,7 +220,8 @@ __device__ __forceinline__ bool ff_edge(unsigned Dsrc, unsigned Ddst, long long 
 // ff words: [0] barrier count, [1] barrier generation, [2 + s] changed in sweep s
 // Run by a group of G CTAs, this one being number lb of the group.
 __device__ void floodfill_body(uint8_t* md, const uint16_t* __restrict__ depth, int H, int W, long long theta_ppm,
-                               unsigned* ff, int max_sweeps, unsigned* status, int lb, int G) {
+                               unsigned* ff, int max_sweeps, unsigned* status, long long spin_limit,
+                               unsigned bar_extra, int lb, int G) {
   __shared__ uint8_t sm[kFFH + 2][kFFW + 2];
   __shared__ uint16_t sd[kFFH + 2][kFFW + 2];
   const int tiles_x = (W + kFFW - 1) / kFFW, tiles_y = (H + kFFH - 1) / kFFH;
@@ -261,7 +262,7 @@ __device__ void floodfill_body(uint8_t* md, const uint16_t* __restrict__ depth, 
       if (grew) md[v * W + u] = 1;
       if (__syncthreads_or(grew) && threadIdx.x == 0) atomicExch(changed + sweep, 1u);
     }
-    if (!grid_barrier(bar, G, status)) return;
+    if (!grid_barrier(bar, G, status, spin_limit, bar_extra)) return;
     if (*(volatile unsigned*)(changed + sweep) == 0u) return;
   }
   if (lb == 0 && threadIdx.x == 0) atomicOr(status, ST_NOT_CONVERGED);
@@ -269,9 +270,10 @@ __device__ void floodfill_body(uint8_t* md, const uint16_t* __restrict__ depth, 
 
 __global__ void __launch_bounds__(kFFThreads) k_floodfill(uint8_t* md, const uint16_t* __restrict__ depth, int H,
                                                            int W, long long theta_ppm, unsigned* ff, int max_sweeps,
-                                                           unsigned* status, const int* gate) {
+                                                           unsigned* status, const int* gate, long long spin_limit,
+                                                           unsigned bar_extra) {
   if (gated_off(gate, kModeTrack)) return;  // uniform over the grid: before any barrier
-  floodfill_body(md, depth, H, W, theta_ppm, ff, max_sweeps, status, blockIdx.x, gridDim.x);
+  floodfill_body(md, depth, H, W, theta_ppm, ff, max_sweeps, status, spin_limit, bar_extra, blockIdx.x, gridDim.x);
 }
 
 // The flood fills of several streams in one cooperative launch: CTA b runs
@@ -283,8 +285,8 @@ __global__ void __launch_bounds__(kFFThreads) k_floodfill_batch(const FloodDesc*
   const int s = cta_stream[blockIdx.x];
   if (s < 0) return;
   const FloodDesc d = descs[s];
-  floodfill_body(d.md, d.depth, d.H, d.W, d.theta_ppm, d.ff, d.max_sweeps, d.status, blockIdx.x - first[s],
-                 first[s + 1] - first[s]);
+  floodfill_body(d.md, d.depth, d.H, d.W, d.theta_ppm, d.ff, d.max_sweeps, d.status, d.spin_limit, d.bar_extra,
+                 blockIdx.x - first[s], first[s + 1] - first[s]);
 }
 
 }  // namespace
@@ -319,7 +321,8 @@ rf_status launch_mask_ff(rf_volume* vol, const DevFrame& f, cudaStream_t st) {
   cfg.numAttrs = 1;
   return check_cuda(vol,
                     cudaLaunchKernelEx(&cfg, k_floodfill, vol->d_md, f.depth, f.H, f.W, vol->dp.theta_ppm, vol->d_ff,
-                                       vol->p.max_ff_sweeps, vol->d_status, f.gate),
+                                       vol->p.max_ff_sweeps, vol->d_status, f.gate, vol->wait_spins,
+                                       vol->wait_extra),
                     "flood-fill launch");
 }
 
@@ -374,6 +377,8 @@ FloodDesc make_flood_desc(rf_volume* vol, const DevFrame& f) {
   d.ff = vol->d_ff;
   d.max_sweeps = vol->p.max_ff_sweeps;
   d.status = vol->d_status;
+  d.spin_limit = vol->wait_spins;
+  d.bar_extra = vol->wait_extra;
   return d;
 }
 
@@ -485,7 +490,8 @@ extern "C" rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* fra
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if ((s = check_cuda(vol, cudaLaunchKernelEx(&cfg, k_floodfill, md, f.depth, f.H, f.W, vol->dp.theta_ppm, ff,
-                                              sweeps, vol->d_status, (const int*)nullptr),
+                                              sweeps, vol->d_status, (const int*)nullptr, vol->wait_spins,
+                                              vol->wait_extra),
                       "flood-fill launch")))
     return s;
   k_dilate<<<blocks, 256, 0, st>>>(md, f.H, f.W, mask_dev, nullptr);

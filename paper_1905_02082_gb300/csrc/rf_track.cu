@@ -602,7 +602,8 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
         }
         __syncthreads();
       }
-      if (!grid_sync_counter(d.bar, (unsigned)(eval + 1) * (unsigned)G, d.status)) return;
+      if (!grid_sync_counter(d.bar, (unsigned)(eval + 1) * (unsigned)G + d.bar_extra, d.status, d.spin_limit))
+        return;
       // every CTA of the group: FP32 reduction of the chunk partials in a fixed
       // order (lane-strided sums, then a shuffle tree); L1 bypassed
       {
@@ -702,6 +703,8 @@ RegDesc make_reg_desc(rf_volume* vol, const DevFrame& f, const double* T_init, c
   d.max_chunks = vol->max_chunks;
   d.bar = vol->d_regbar;
   d.status = vol->d_status;
+  d.spin_limit = vol->wait_spins;
+  d.bar_extra = vol->wait_extra;
   d.pxcache = vol->d_pxcache;
   return d;
 }

@@ -63,6 +63,10 @@ struct rf_volume {
   bool profiling = false;
   cudaEvent_t ev[rf::EV_COUNT] = {};
 
+  // bounded waits of the grid barriers (rf_set_wait_limits)
+  long long wait_spins = rf::kDefaultSpinLimit;
+  unsigned wait_extra = 0;
+
   // launch shapes (grid = SMs x CTAs per SM), set by rf_set_launch_config
   rf_launch_config launch = {16, 8, 2, 8, 16};
 
