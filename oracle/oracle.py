@@ -74,6 +74,8 @@ def _load():
         lib.orc_integrate.restype = C.c_int64
         lib.orc_integrate.argtypes = [vp, C.POINTER(Frame), dp, u8p]
         lib.orc_track.argtypes = [vp, C.POINTER(Frame), dp, u8p, dp, C.POINTER(TrackInfo)]
+        lib.orc_track_footprint.argtypes = [vp, C.POINTER(Frame), dp, u8p, dp, C.POINTER(TrackInfo),
+                                            C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         lib.orc_eval.argtypes = [vp, C.POINTER(Frame), dp, C.c_int, u8p, dp, dp, dp, C.POINTER(C.c_int64)]
         lib.orc_lookup.restype = C.c_int
         lib.orc_lookup.argtypes = [vp, dp, dp, dp, dp, dp, C.POINTER(C.c_int)]
@@ -189,6 +191,18 @@ class OracleVolume:
         m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
         self.lib.orc_track(self.h, C.byref(f.c), _dptr(T), _vptr(m), _dptr(out), C.byref(info))
         return out, info
+
+    def track_footprint(self, f: FrameData, T_init, mask=None):
+        """track(), plus the distinct blocks probed and voxels read by its
+        model lookups: (T, info, n_blocks, n_voxels)."""
+        T = _T(T_init)
+        out = np.zeros((4, 4))
+        info = TrackInfo()
+        nb, nv = C.c_int64(), C.c_int64()
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        self.lib.orc_track_footprint(self.h, C.byref(f.c), _dptr(T), _vptr(m), _dptr(out), C.byref(info),
+                                     C.byref(nb), C.byref(nv))
+        return out, info, nb.value, nv.value
 
     def eval(self, f: FrameData, T, stride=1, mask=None):
         T = _T(T)

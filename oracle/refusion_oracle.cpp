@@ -51,6 +51,7 @@
 #include <cstring>
 #include <deque>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 typedef __int128 i128;
@@ -90,6 +91,10 @@ struct Volume {
   int frames = 0;
   // integer forms of the parameters
   int64_t v_um, du_um, dmin_um, dmax_um, znear_tick, dmax_tick, tau_tick;
+  // bookkeeping only (no effect on any result): when set, model lookups
+  // record the distinct blocks they probe and voxels they read
+  std::unordered_set<BlockKey, BlockKeyHash>* probed = nullptr;
+  std::unordered_set<int64_t>* read = nullptr;
 };
 
 // floor(a / b) for b > 0
@@ -287,8 +292,10 @@ bool gather(Volume& V, const int64_t k0[3], Corners* c) {
       l[i] = (int)(k[i] - b[i] * BS);
     }
     Block* B = find_block(V, b[0], b[1], b[2]);
+    if (V.probed) V.probed->insert(BlockKey{b[0], b[1], b[2]});
     if (!B) return false;
     int vi = vidx(l[0], l[1], l[2]);
+    if (V.read) V.read->insert((k[0] & 0x1FFFFF) | ((k[1] & 0x1FFFFF) << 21) | ((k[2] & 0x1FFFFF) << 42));
     if (B->W[vi] <= 0) return false;
     c->F[n] = B->F[vi];
     c->I[n] = intensity(B->rgb + 3 * vi);
@@ -843,6 +850,20 @@ int64_t orc_integrate(void* vol, const orc_frame* f, const double T[16], const u
 void orc_track(void* vol, const orc_frame* f, const double T_init[16], const uint8_t* mask, double T_out[16],
                orc_track_info* info) {
   track(*static_cast<Volume*>(vol), f, T_init, mask, T_out, info);
+}
+
+void orc_track_footprint(void* vol, const orc_frame* f, const double T_init[16], const uint8_t* mask,
+                         double T_out[16], orc_track_info* info, int64_t* n_blocks_probed, int64_t* n_voxels_read) {
+  Volume& V = *static_cast<Volume*>(vol);
+  std::unordered_set<BlockKey, BlockKeyHash> probed;
+  std::unordered_set<int64_t> read;
+  V.probed = &probed;
+  V.read = &read;
+  track(V, f, T_init, mask, T_out, info);
+  V.probed = nullptr;
+  V.read = nullptr;
+  *n_blocks_probed = (int64_t)probed.size();
+  *n_voxels_read = (int64_t)read.size();
 }
 
 void orc_eval(void* vol, const orc_frame* f, const double T[16], int stride, const uint8_t* mask, double H[21],

@@ -66,6 +66,11 @@ int64_t orc_integrate(void* vol, const orc_frame* f, const double T[16], const u
 /* Levenberg-Marquardt registration (three levels). */
 void orc_track(void* vol, const orc_frame* f, const double T_init[16], const uint8_t* mask,
                double T_out[16], orc_track_info* info);
+/* orc_track, also counting the distinct blocks its model lookups probed and
+ * the distinct voxels they read (the footprint of a registration; bookkeeping
+ * only, the result is orc_track's). */
+void orc_track_footprint(void* vol, const orc_frame* f, const double T_init[16], const uint8_t* mask,
+                         double T_out[16], orc_track_info* info, int64_t* n_blocks_probed, int64_t* n_voxels_read);
 
 /* Normal equations at pose T: H[21] (upper triangle, row-major), g[6], E, N. */
 void orc_eval(void* vol, const orc_frame* f, const double T[16], int stride, const uint8_t* mask,

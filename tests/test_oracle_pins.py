@@ -878,3 +878,28 @@ def test_tracking_recovers_an_exact_minimiser(oracle_mod):
         assert np.linalg.norm(T[:3, 3]) < 1e-8, T[:3, 3]
         assert rot_err(T[:3, :3], np.eye(3)) < 1e-8
         assert info.evals >= 4
+
+
+def test_tracking_footprint_fixture_matches_the_oracle(oracle_mod):
+    """The stored registration footprint (tests/golden/track_footprint_static.json,
+    written by make_track_footprint.py from the oracle alone) is what the
+    oracle counts now, on the first frame's two registrations; counting does
+    not change the registration's result."""
+    O = oracle_mod
+    from synth import make_sequence
+    g = json.load(open(os.path.join(GOLDEN, "track_footprint_static.json")))
+    seq = make_sequence("static", 1000)
+    cam = seq.camera
+    vol = O.OracleVolume(voxel_size=0.01, trunc=0.1)
+    d, rgb, T, _ = seq.frame(0)
+    vol.integrate(_frame(O, d, rgb, cam), T)
+    d, rgb, _, _ = seq.frame(1)
+    f = _frame(O, d, rgb, cam)
+    T1, _, b1, v1 = vol.track_footprint(f, T)
+    T1_plain, _ = vol.track(f, T)
+    np.testing.assert_array_equal(T1, T1_plain)
+    mask = vol.compute_mask(f, T1)
+    _, _, b2, v2 = vol.track_footprint(f, T1, mask)
+    rows = [r for r in g["rows"] if r["frame"] == 1]
+    assert [(r["blocks_probed"], r["voxels_read"]) for r in rows] == [(b1, v1), (b2, v2)]
+    assert 0 < b1 < vol.num_blocks and 0 < v1 < 512 * b1
