@@ -60,7 +60,7 @@ typedef enum rf_status {
  * 0.01 m, tau 0.1 m, w_c 0.025, theta 0.007, gamma 0.5) and the readings
  * for the quantities the paper leaves open. */
 typedef struct rf_params {
-  double voxel_size;   /* metres; voxel_size * 1e6 must be an integer (micrometre lattice) */
+  double voxel_size;   /* metres, at most 0.15; voxel_size * 1e6 must be an integer (micrometre lattice) */
   double trunc;        /* truncation distance tau (Sec. III-A), metres */
   double w_c;          /* colour weight w_c of Eq. 4 */
   double theta;        /* flood-fill depth threshold of Alg. 1 (used as round(theta*1e6) ppm) */

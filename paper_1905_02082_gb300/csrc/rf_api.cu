@@ -97,8 +97,9 @@ rf_status dalloc(rf_volume* vol, T** p, size_t count, const char* what) {
 bool is_integer(double x) { return std::fabs(x - std::llround(x)) < 1e-6; }
 
 rf_status validate_params(const rf_params* p) {
-  if (!(p->voxel_size > 0.0 && p->voxel_size <= 1.0) || !is_integer(p->voxel_size * 1e6))
-    return set_error(nullptr, RF_ERR_INVALID_ARG, "voxel_size must be a positive whole number of micrometres");
+  if (!(p->voxel_size > 0.0 && p->voxel_size <= 0.15) || !is_integer(p->voxel_size * 1e6))
+    return set_error(nullptr, RF_ERR_INVALID_ARG,
+                     "voxel_size must be a positive whole number of micrometres, at most 0.15 m");
   if (!(p->trunc > 0.0 && p->trunc < 10.0)) return set_error(nullptr, RF_ERR_INVALID_ARG, "trunc out of range");
   if (!(p->depth_scale > 0.0) || !is_integer(1e6 / p->depth_scale))
     return set_error(nullptr, RF_ERR_INVALID_ARG, "1e6/depth_scale must be an integer");
@@ -151,6 +152,7 @@ rf_status volume_buffers(rf_volume* vol, const rf_params* p, int64_t n_buckets, 
       (s = A(&vol->d_partials, 2 * 29 * max_chunks + 2, "partials")) || (s = A(&vol->d_seeds, npix, "seeds")) ||
       (s = A(&vol->d_md, npix, "mask work")) || (s = A(&vol->d_ff, (size_t)p->max_ff_sweeps + 2, "flood-fill words")) ||
       (s = A(&vol->d_integ, 1, "integ")) || (s = A(&vol->d_tilemax, ntiles, "tiles")) ||
+      (s = A(&vol->d_dmask, npix, "masked depth")) ||
       (s = A(&vol->d_cand, (size_t)p->max_candidates, "candidates")) || (s = A(&vol->d_depth, npix, "depth staging")) ||
       (s = A(&vol->d_rgb, npix * 3, "rgb staging")) || (s = A(&vol->d_mask, npix, "mask staging")) ||
       (s = A(&vol->d_T, 48, "poses")) || (s = A(&vol->d_info, 1, "info")) || (s = A(&vol->d_guard, 1, "guard count")) ||
@@ -186,6 +188,7 @@ DevParams derive(const rf_params& p) {
   d.theta_ppm = llround(p.theta * 1e6);
   d.storage = p.storage;
   d.inv_tau = (float)(1.0 / p.trunc);
+  d.du_tick = (unsigned)(d.du_um * 1024);
   return d;
 }
 
@@ -639,7 +642,7 @@ rf_status rf_destroy_volume(rf_volume* vol) {
   void* dev[] = {vol->d_hash, vol->d_vox,  vol->d_W,       vol->d_coords, vol->d_nbr, vol->d_nblocks, vol->d_status,
                  vol->d_regbar, vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
                  vol->d_tilemax, vol->d_cand, vol->d_depth, vol->d_rgb,   vol->d_mask,    vol->d_T, vol->d_info,
-                 vol->d_guard, vol->d_pxcache};
+                 vol->d_guard, vol->d_pxcache, vol->d_dmask};
   for (void* p : dev)
     if (p) cudaFree(p);
   delete vol;

@@ -30,9 +30,10 @@ namespace rf {
 namespace {
 
 // Quantised pose (one entry per lane: conversions run on the FP64 pipe, so
-// they are spread over lanes) and reset of the per-frame counters.
+// they are spread over lanes), the per-frame constants of the voxel loop and
+// the reset of the per-frame counters.
 __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const int* __restrict__ n_blocks,
-                             const int* gate) {
+                             DevParams p, const int* gate) {
   if (gated_off(gate, kModeFirst)) return;
   const int a = threadIdx.x;
   if (a < 9) {
@@ -51,11 +52,24 @@ __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const
     st->new_blocks = 0;
     st->updated = 0ull;
     st->pool_before = *n_blocks;
+  } else if (a < 21) {
+    // camera z of voxel step z (z = a - 13) in 2^-20 ticks, split exactly
+    const long long zs = (a - 13) * (llround(T[10] * 1073741824.0) * p.v_um);
+    st->qz[a - 13] = (int)(zs >> 20);
+    st->rz[a - 13] = (int)(zs & 0xFFFFF);
+  } else if (a < 24) {
+    // one voxel step along world z, camera coordinate i = a - 21, in ticks
+    const int i = a - 21;
+    st->szf[i] = (float)((double)(llround(T[8 + i] * 1073741824.0) * p.v_um) * (1.0 / 1048576.0));
   }
 }
 
+// Per 16x16 tile: the largest valid unmasked depth (frustum search), and the
+// frame's depth with invalid and masked pixels zeroed (the per-voxel loop
+// then tests one value per pixel).
 __global__ void __launch_bounds__(256) k_tilemax(DevFrame f, DevParams p, const uint8_t* __restrict__ mask,
-                                                 int* __restrict__ tilemax, IntegState* st, int tiles_x) {
+                                                 int* __restrict__ tilemax, IntegState* st, int tiles_x,
+                                                 uint16_t* __restrict__ dm) {
   if (gated_off(f.gate, kModeFirst)) return;
   const int tile = blockIdx.x;
   const int u = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
@@ -64,7 +78,9 @@ __global__ void __launch_bounds__(256) k_tilemax(DevFrame f, DevParams p, const 
   if (u < f.W && v < f.H) {
     const int idx = v * f.W + u;
     const unsigned raw = f.depth[idx];
-    if (pixel_valid(p, raw) && !(mask && mask[idx])) d = (int)(raw * p.du_um);
+    const bool use = pixel_valid(p, raw) && !(mask && mask[idx]);
+    if (use) d = (int)(raw * p.du_um);
+    dm[idx] = use ? (uint16_t)raw : (uint16_t)0;
   }
   d = __reduce_max_sync(0xffffffffu, d);
   __shared__ int s[8];
@@ -229,10 +245,173 @@ __global__ void __launch_bounds__(256) k_cull(DevFrame f, DevParams p, IntegStat
   }
 }
 
+constexpr int kIntegThreads = 128;  // 4 warps; one warp integrates one block at a time
+constexpr int kIntegWarps = kIntegThreads / 32;
+constexpr float kTickMetres = 9.765625e-10f;  // 2^-10 um
+
+// Colour running average of one band voxel (Sec. III-A, reading: RGB8 kept
+// rounded half up, own weight Wc): (Wc C + c) / (Wc + 1) per channel as an
+// exact integer quotient from a float reciprocal, corrected one step either way.
+__device__ __forceinline__ unsigned colour_update(unsigned word, const uint8_t* c, int w_max) {
+  const unsigned wc = word >> 24;
+  const unsigned den = 2 * (wc + 1);
+  const float rden = __frcp_rn((float)den);
+  unsigned out = 0;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    const unsigned num = 2 * (wc * ((word >> (8 * ch)) & 255u) + __ldg(c + ch)) + wc + 1;
+    unsigned q = (unsigned)((float)num * rden);
+    if (q * den > num) q -= 1;
+    else if ((q + 1) * den <= num) q += 1;
+    out |= q << (8 * ch);
+  }
+  return out | (min(wc + 1, (unsigned)w_max) << 24);
+}
+
+// Float of an int64 count of 2^-20 ticks, in ticks, without the FP64 pipe:
+// the two 32-bit halves are converted separately (error below 2^-12 ticks plus
+// one float rounding).
+__device__ __forceinline__ float ticks_f(long long s) {
+  const float hi = (float)(int)(s >> 32), lo = (float)(unsigned)(s & 0xffffffffll);
+  return fmaf(hi, 4096.0f, lo * 9.5367431640625e-07f);  // hi 2^32 / 2^20, lo / 2^20
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Floor of a pixel estimate and whether it lies within `amb` of a rounding
+// boundary (the exact integer path then decides).  Adding 1.5 * 2^23 rounds a
+// float below 2^22 in magnitude to an integer in the low mantissa bits, so
+// floor(e) = round(e - 1/2) costs a few FP32 adds and no conversion.
+__device__ __forceinline__ int pixel_floor(float est, float amb, bool& ambiguous) {
+  const float e = fminf(fmaxf(est, -4194304.0f), 4194304.0f);
+  const float t = (e - 0.5f) + 12582912.0f;
+  const float fr = e - (t - 12582912.0f);
+  ambiguous = fabsf(fr - 0.5f) > 0.5f - amb;
+  return __float_as_int(t) - 0x4B400000;
+}
+
+// Everything the voxel loop of one frame needs (shared memory, per CTA).
+struct IntegShared {
+  long long A[9], tq[3];
+  float szf[3];
+  int qz[8], rz[8];
+  float rcpw[256];  // 1 / (W + 1), W = 0..255 (running-average divisor)
+};
+
+// Per-lane constants: lane l owns voxels (x, y, z) = (l & 7, (l >> 3) + 4 h, z),
+// h = 0, 1, z = 0..7, i.e. block indices l + 32 h + 64 z.  Their offsets from
+// the block origin in camera coordinates: float estimates lf (ticks) and, for
+// camera z, the exact split ql * 2^20 + rl of the 2^-20-tick sum.
+struct LaneConsts {
+  float lf[3][2];
+  int ql[2], rl[2];
+};
+
+__device__ __forceinline__ void lane_consts(const IntegShared& sh, long long v_um, int lane, LaneConsts& c) {
+  const long long x = (long long)(lane & 7) * v_um;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const long long y = (long long)((lane >> 3) + 4 * h) * v_um;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const long long L = sh.A[i * 3] * x + sh.A[i * 3 + 1] * y;
+      c.lf[i][h] = ticks_f(L);
+      if (i == 2) {
+        c.ql[h] = (int)(L >> 20);
+        c.rl[h] = (int)(L & 0xFFFFF);
+      }
+    }
+  }
+}
+
+// Per-block state: origin voxel (0, 0, 0) of block b in camera coordinates.
+struct BlockState {
+  long long* S;    // exact sums, 2^-20 ticks (the warp's shared memory)
+  long long Qb;    // floor(S_z / 2^20): camera z of the origin in ticks
+  float base[3][2];  // float estimates of the lane's two voxel columns at z = 0
+  int rbl[2];        // remainder of S_z plus the lane's column remainder
+  int ql[2];         // the lane's column offsets: whole ticks of camera z
+  int zlo, zhi;      // z range (z_near, d_max] in ticks relative to Qb
+};
+
+__device__ __forceinline__ int clamp32(long long v) {
+  return (int)max(min(v, 2147483647ll), -2147483647ll);
+}
+
+// lc: this thread's LaneConsts (shared memory); S: the warp's 3 shared words.
+__device__ __forceinline__ void block_state(const IntegShared& sh, const DevParams& p, const LaneConsts& lc, int4 b,
+                                            long long* S, int lane, BlockState& bs) {
+  const long long d0 = (long long)b.x * 8 * p.v_um - sh.tq[0], d1 = (long long)b.y * 8 * p.v_um - sh.tq[1],
+                  d2 = (long long)b.z * 8 * p.v_um - sh.tq[2];
+  long long s2 = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const long long si = sh.A[i * 3] * d0 + sh.A[i * 3 + 1] * d1 + sh.A[i * 3 + 2] * d2;
+    if (lane == i) S[i] = si;
+    if (i == 2) s2 = si;
+    const float bf = ticks_f(si);
+    bs.base[i][0] = bf + lc.lf[i][0];
+    bs.base[i][1] = bf + lc.lf[i][1];
+  }
+  bs.S = S;
+  bs.Qb = s2 >> 20;
+  const int rb = (int)(s2 & 0xFFFFF);
+  bs.rbl[0] = rb + lc.rl[0];
+  bs.rbl[1] = rb + lc.rl[1];
+  bs.ql[0] = lc.ql[0];
+  bs.ql[1] = lc.ql[1];
+  bs.zlo = clamp32(p.znear_tick - bs.Qb);
+  bs.zhi = clamp32(p.dmax_tick - bs.Qb);
+  __syncwarp();
+}
+
+// Update value of a voxel given its pixel's masked raw depth and its camera
+// z (Qb + dz): false when not updated (invalid or masked pixel, or occluded:
+// sdf < -tau).  sdf = D - z exactly in ticks; |sdf| <= tau: the band.
+__device__ __forceinline__ bool sdf_value(unsigned raw, long long Qb, int dz, const DevParams& p, float& x,
+                                          bool& band) {
+  if (raw == 0u) return false;
+  const long long sdf = (long long)raw * p.du_tick - Qb - dz;
+  if (sdf < -p.tau_tick) return false;
+  band = sdf <= p.tau_tick;
+  x = !band ? p.tau
+            : (p.tau_tick < (1ll << 31) ? (float)(int)sdf * kTickMetres : (float)(int)(sdf >> 8) * 2.5e-7f);
+  return true;
+}
+
+// Fast decision of voxel (lane, h, z): -1 when not updated, kAmbiguous when
+// the float pixel estimate is too close to a rounding boundary, else the
+// pixel index (bit 31 set inside the band) and *x the update value.
+constexpr int kAmbiguous = -2;
+__device__ __forceinline__ int decide_fast(const IntegShared& sh, const BlockState& bs, const DevFrame& f, const DevParams& p, float fxg, float fyg, float cxg,
+                                           float cyg, const uint16_t* __restrict__ dm, int h, int z, float zr,
+                                           float& x) {
+  // per-column values selected, not indexed (h is not a compile-time constant)
+  const int t = (h ? bs.rbl[1] : bs.rbl[0]) + sh.rz[z];
+  const int dz = (h ? bs.ql[1] : bs.ql[0]) + sh.qz[z] + (t >> 20);
+  if (!(dz > bs.zlo && dz <= bs.zhi)) return -1;
+  const float zf = fmaf(zr, sh.szf[2], h ? bs.base[2][1] : bs.base[2][0]);  // zr = (float)z
+  const float xf = fmaf(zr, sh.szf[0], h ? bs.base[0][1] : bs.base[0][0]);
+  const float yf = fmaf(zr, sh.szf[1], h ? bs.base[1][1] : bs.base[1][0]);
+  const float iz = rcp_approx(zf);
+  bool au, av;
+  const int u = pixel_floor(fmaf(fxg * xf, iz, cxg), f.amb_u, au);
+  const int v = pixel_floor(fmaf(fyg * yf, iz, cyg), f.amb_v, av);
+  if (au || av) return kAmbiguous;
+  if ((unsigned)u >= (unsigned)f.W || (unsigned)v >= (unsigned)f.H) return -1;
+  const int pix = v * f.W + u;
+  bool band = false;
+  if (!sdf_value(__ldg(dm + pix), bs.Qb, dz, p, x, band)) return -1;
+  return band ? (pix | (int)0x80000000) : pix;
+}
+
 // floor(num / den) for den > 0 when it lies in [0, n), else -1.  `guess` is
 // a float estimate of num / den (within one unit when the result is in
-// range); it is corrected and verified with exact int64 products.  No
-// int64 <-> float conversion is used: those run on the FP64 pipe.
+// range); it is corrected and verified with exact int64 products.
 __device__ __forceinline__ int pixel_of(float guess, long long num, long long den, int n) {
   const float g = fminf(fmaxf(floorf(guess), -2.0f), (float)n + 1.0f);
   long long u = (long long)(int)g;
@@ -242,48 +421,33 @@ __device__ __forceinline__ int pixel_of(float guess, long long num, long long de
   return (u >= 0 && u < n) ? (int)u : -1;
 }
 
-// Exact nearest pixel of a voxel with camera coordinates (Cx, Cy, Cz) in
-// ticks, or -1 when z is outside (z_near, d_max] or the pixel is outside the
-// image.  (xf, yf, zf): float estimates used only for the guess.
-__device__ __forceinline__ int voxel_pixel(long long Cx, long long Cy, long long Cz, float xf, float yf, float zf,
-                                           const DevFrame& f, const DevParams& p, float fxg, float fyg, float cxg,
-                                           float cyg) {
-  if (Cz <= p.znear_tick || Cz > p.dmax_tick) return -1;
-  const long long den = Cz << 8;
-  const float iz = __fdividef(1.0f, zf);
-  const int u = pixel_of(fxg * xf * iz + cxg, f.fxq * Cx + f.cxq * Cz, den, f.W);
-  if (u < 0) return -1;
-  const int v = pixel_of(fyg * yf * iz + cyg, f.fyq * Cy + f.cyq * Cz, den, f.H);
-  if (v < 0) return -1;
-  return v * f.W + u;
-}
-
-// Fast path of the nearest-pixel rounding: floor of the float estimate when
-// it is farther than `amb` from a rounding boundary (then provably equal to
-// the exact floor), else kAmbiguous.  Out-of-range results give -1.
-constexpr int kAmbiguous = -2;
-__device__ __forceinline__ int pixel_fast(float est, float amb, int n) {
-  const float fl = floorf(est);
-  const float fr = est - fl;
-  if (fr < amb || fr > 1.0f - amb) return kAmbiguous;
-  return (fl >= 0.0f && fl < (float)n) ? (int)fl : -1;
-}
-
-// Update value of a voxel whose pixel has raw depth `raw`: false when the
-// voxel is not updated (invalid pixel or occluded: sdf < -tau).
-__device__ __forceinline__ bool voxel_value(unsigned raw, long long Cz, const DevParams& p, float* x, bool* band) {
-  if (!pixel_valid(p, raw)) return false;
-  const long long sdf = (long long)raw * p.du_um * 1024 - Cz;
-  if (sdf < -p.tau_tick) return false;
-  *band = sdf <= p.tau_tick;
-  if (*band) {
-    // |sdf| <= tau_tick: a 32-bit conversion (exact below 2^31 ticks = 2.1 m)
-    *x = p.tau_tick < (1ll << 31) ? __int2float_rn((int)sdf) * 9.765625e-10f
-                                  : __int2float_rn((int)(sdf >> 8)) * 2.5e-7f;
-  } else {
-    *x = p.tau;
+// Exact decision of voxel (x, y, z) of the block: camera coordinates
+// C = floor(S / 2^20) from int64 sums, pixel u = floor((fxq Cx + cxq Cz) /
+// (256 Cz)) verified with int64 products.  Same return convention as
+// decide_fast.  Taken for the few voxels whose estimate is ambiguous.
+__device__ int decide_exact(const IntegShared& sh, const BlockState& bs, const DevFrame& f, const DevParams& p,
+                            float fxg, float fyg, float cxg, float cyg, const uint16_t* __restrict__ dm, int vx,
+                            int vy, int vz, float& x) {
+  long long C[3];
+  float cf[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const long long s = bs.S[i] + sh.A[i * 3] * (vx * p.v_um) + sh.A[i * 3 + 1] * (vy * p.v_um) +
+                        sh.A[i * 3 + 2] * (vz * p.v_um);
+    C[i] = s >> 20;
+    cf[i] = ticks_f(s);
   }
-  return true;
+  if (C[2] <= p.znear_tick || C[2] > p.dmax_tick) return -1;
+  const long long den = C[2] << 8;
+  const float iz = __frcp_rn(cf[2]);
+  const int u = pixel_of(fxg * cf[0] * iz + cxg, f.fxq * C[0] + f.cxq * C[2], den, f.W);
+  if (u < 0) return -1;
+  const int v = pixel_of(fyg * cf[1] * iz + cyg, f.fyq * C[1] + f.cyq * C[2], den, f.H);
+  if (v < 0) return -1;
+  const int pix = v * f.W + u;
+  bool band = false;
+  if (!sdf_value(__ldg(dm + pix), bs.Qb, (int)(C[2] - bs.Qb), p, x, band)) return -1;
+  return band ? (pix | (int)0x80000000) : pix;
 }
 
 // Lookup-or-insert of a block; only called for blocks no other CTA of the
@@ -324,131 +488,71 @@ __device__ int hash_insert(const DevVol& v, int bx, int by, int bz, bool* is_new
   return -1;
 }
 
-constexpr int kIntegThreads = 128;  // 4 warps; one warp integrates one block at a time
-constexpr int kIntegWarps = kIntegThreads / 32;
-constexpr int kVPL = kBV / 32;       // 16 voxels per lane: voxel lane + 32 j
-
-// Colour running average of one band voxel (Sec. III-A, reading: RGB8 kept
-// rounded half up, own weight Wc): (Wc C + c) / (Wc + 1) per channel as an
-// exact integer quotient from a float reciprocal, corrected one step either way.
-__device__ __forceinline__ unsigned colour_update(unsigned word, const uint8_t* c, int w_max) {
-  const unsigned wc = word >> 24;
-  const unsigned den = 2 * (wc + 1);
-  const float rden = __frcp_rn((float)den);
-  unsigned out = 0;
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    const unsigned num = 2 * (wc * ((word >> (8 * ch)) & 255u) + __ldg(c + ch)) + wc + 1;
-    unsigned q = (unsigned)((float)num * rden);
-    if (q * den > num) q -= 1;
-    else if ((q + 1) * den <= num) q += 1;
-    out |= q << (8 * ch);
-  }
-  return out | (min(wc + 1, (unsigned)w_max) << 24);
+// Running-average update of one voxel (Sec. III-A; free space, Sec. III-D:
+// value tau).  FP32 storage: the uint2 word {F, RGB | Wc << 24} and the
+// weight byte.  dec: decide_* result (>= 0: updated).
+__device__ __forceinline__ void update_fp32(uint2& w, unsigned& W, int dec, float x, const IntegShared& sh,
+                                            const uint8_t* __restrict__ rgb, int w_max) {
+  const float F = __uint_as_float(w.x);
+  const float Wf = __uint_as_float(0x4B000000u | W) - 8388608.0f;  // exact float of W <= 255
+  const float Fn = W == 0u ? x : fmaf(Wf, F, x) * sh.rcpw[W];
+  w.x = __float_as_uint(Fn);
+  if (dec < 0) w.y = colour_update(w.y, rgb + 3 * (size_t)(dec & 0x7fffffff), w_max);  // band
+  W = min(W + 1u, (unsigned)w_max);
 }
 
-// Per-lane constants of the voxel loop for one stream: lane l's offsets
-// within a block (from the quantised rotation) and the intrinsics in pixels.
-struct IntegConsts {
-  long long O[3], SY4[3], SZ[3];
-  float SY4f[3], SZf[3];
-  float fxg, fyg, cxg, cyg;
-};
-
-__device__ __forceinline__ void integ_consts(const long long* A, const DevFrame& f, const DevParams& p, int lane,
-                                             IntegConsts& c) {
-  const long long lx = (long long)(lane & 7) * p.v_um, ly = (long long)(lane >> 3) * p.v_um;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    c.O[i] = A[i * 3] * lx + A[i * 3 + 1] * ly;
-    c.SY4[i] = A[i * 3 + 1] * (4 * p.v_um);
-    c.SZ[i] = A[i * 3 + 2] * p.v_um;
-    c.SY4f[i] = (float)(c.SY4[i] >> 20);  // float estimates in ticks, converted once per thread
-    c.SZf[i] = (float)(c.SZ[i] >> 20);
+// FP16 storage: tracking word {F16(F / tau) | I8 << 16 | W << 24} always,
+// colour word {RGB | Wc << 24} inside the band (I8 derived from the colour).
+__device__ __forceinline__ void update_fp16(unsigned& t, unsigned& col, bool& col_written, int dec, float x,
+                                            const IntegShared& sh, const uint8_t* __restrict__ rgb,
+                                            const DevParams& p) {
+  const unsigned W = t >> 24;
+  const float F = __half2float(__ushort_as_half((unsigned short)(t & 0xFFFFu))) * p.tau;
+  const float Wf = __uint_as_float(0x4B000000u | W) - 8388608.0f;
+  const float Fn = W == 0u ? x : fmaf(Wf, F, x) * sh.rcpw[W];
+  const unsigned h = (unsigned)__half_as_ushort(__float2half_rn(Fn * p.inv_tau));
+  unsigned i8 = (t >> 16) & 255u;
+  if (dec < 0) {  // band: colour, and the intensity derived from it
+    col = colour_update(col, rgb + 3 * (size_t)(dec & 0x7fffffff), p.w_max);
+    col_written = true;
+    i8 = rgb_i8(col);
   }
-  c.fxg = (float)f.fxq * (1.0f / 256.0f);
-  c.fyg = (float)f.fyq * (1.0f / 256.0f);
-  c.cxg = (float)f.cxq * (1.0f / 256.0f);
-  c.cyg = (float)f.cyq * (1.0f / 256.0f);
+  t = h | (i8 << 16) | (min(W + 1u, (unsigned)p.w_max) << 24);
 }
 
-// One candidate block b, integrated by one warp.  Lane l owns voxels
-// (x, y, z) = (l & 7, (l >> 3) + 4 (j & 1), j >> 1), j = 0..15, whose exact
-// camera coordinates follow from the block's by int64 additions.  (1) nearest
-// pixels of the 16 voxels (float estimate, exact integer path only near
-// rounding boundaries), (2) depth loads four at a time and the exact
-// truncation tests, (3) hash lookup (first bucket prefetched by lanes 0-3) or
-// insert, (4) read-modify-write of the updated voxels.  Per-voxel values are
-// staged in the warp's shared memory (spx, sx), not registers.  A and tq: the
-// quantised pose (shared memory).
+// One candidate block b, integrated by one warp (see k_integrate).
 template <int ST>
 __device__ __forceinline__ void integrate_block(const DevVol& v, const DevFrame& f, const DevParams& p,
-                                                const uint8_t* __restrict__ mask, const long long* A,
-                                                const long long* tq, const IntegConsts& c, const int4 b, int lane,
-                                                int (*spx)[32], float (*sx)[32], unsigned& my_updated,
-                                                unsigned& my_new) {
-  const unsigned nan_bits = 0x7fc00000u;
+                                                const uint16_t* __restrict__ dm, const IntegShared& sh,
+                                                const LaneConsts& lc, const int4 b, int lane, unsigned short* aq,
+                                                long long* S, unsigned& my_updated, unsigned& my_new) {
   const unsigned long long key = pack_key(b.x, b.y, b.z);
   const bool in_range = coord_ok(b.x, b.y, b.z);
   const unsigned long long bucket = bucket_of(key, v.bucket_mask);
   unsigned long long e = kEmpty;
-  if (lane < kSlots && in_range) e = __ldcg(v.hash + bucket * kSlots + lane);  // prefetch
-  // exact camera coordinates of voxel (lane & 7, lane >> 3, 0) of this block
-  long long c0[3];
-  float c0f[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const long long d0 = (long long)b.x * 8 * p.v_um - tq[0], d1 = (long long)b.y * 8 * p.v_um - tq[1],
-                    d2 = (long long)b.z * 8 * p.v_um - tq[2];
-    c0[i] = A[i * 3] * d0 + A[i * 3 + 1] * d1 + A[i * 3 + 2] * d2 + c.O[i];
-    c0f[i] = (float)(c0[i] >> 20);
-  }
-  // 1) nearest pixel of each voxel
-#pragma unroll 2
-  for (int j = 0; j < kVPL; ++j) {
-    const int h = j & 1, zz = j >> 1;
-    const long long Cz = (c0[2] + (h ? c.SY4[2] : 0ll) + zz * c.SZ[2]) >> 20;
-    int pix = -1;
-    if (Cz > p.znear_tick && Cz <= p.dmax_tick) {
-      const float xf = c0f[0] + (h ? c.SY4f[0] : 0.0f) + (float)zz * c.SZf[0];
-      const float yf = c0f[1] + (h ? c.SY4f[1] : 0.0f) + (float)zz * c.SZf[1];
-      const float zf = c0f[2] + (h ? c.SY4f[2] : 0.0f) + (float)zz * c.SZf[2];
-      const float iz = __frcp_rn(zf);
-      const int u = pixel_fast(c.fxg * xf * iz + c.cxg, f.amb_u, f.W);
-      const int vv = pixel_fast(c.fyg * yf * iz + c.cyg, f.amb_v, f.H);
-      pix = (u == kAmbiguous || vv == kAmbiguous) ? kAmbiguous : ((u < 0 || vv < 0) ? -1 : vv * f.W + u);
-      if (pix == kAmbiguous) {
-        const long long Cx = (c0[0] + (h ? c.SY4[0] : 0ll) + zz * c.SZ[0]) >> 20;
-        const long long Cy = (c0[1] + (h ? c.SY4[1] : 0ll) + zz * c.SZ[1]) >> 20;
-        pix = voxel_pixel(Cx, Cy, Cz, xf, yf, zf, f, p, c.fxg, c.fyg, c.cxg, c.cyg);
-      }
-    }
-    spx[j][lane] = pix;
-  }
-  // 2) depth (and mask) loads, four voxels at a time, and the exact tests
-  unsigned passbits = 0;
-#pragma unroll 4
-  for (int j = 0; j < kVPL; ++j) {
-    const int pix = spx[j][lane];
-    unsigned raw = pix >= 0 ? (unsigned)__ldg(f.depth + pix) : 0u;
-    if (mask && pix >= 0 && __ldg(mask + pix)) raw = 0u;  // masked pixel: as invalid
-    const int h = j & 1, zz = j >> 1;
-    const long long Cz = (c0[2] + (h ? c.SY4[2] : 0ll) + zz * c.SZ[2]) >> 20;
-    float x = 0.0f;
-    bool band = false;
-    const bool ok = pix >= 0 && voxel_value(raw, Cz, p, &x, &band);
-    sx[j][lane] = x;
-    if (band) spx[j][lane] = pix | (int)0x80000000;
-    passbits |= ok ? (1u << j) : 0u;
-  }
-  if (!__any_sync(0xffffffffu, passbits != 0)) return;
-  // 3) pool index: from the prefetched bucket, else probe/insert by lane 0
+  if (lane < kSlots && in_range) e = __ldcg(v.hash + bucket * kSlots + lane);  // first bucket
+  const float fxg = (float)f.fxq * (1.0f / 256.0f), fyg = (float)f.fyq * (1.0f / 256.0f);
+  const float cxg = (float)f.cxq * (1.0f / 256.0f), cyg = (float)f.cyq * (1.0f / 256.0f);
+  BlockState bs;
+  block_state(sh, p, lc, b, S, lane, bs);
   const unsigned found = __ballot_sync(0xffffffffu, lane < kSlots && e != kEmpty && (e >> 22) == key);
-  int pool;
+  int pool = -1;
   bool fresh = false;
   if (found) {
     pool = (int)(__shfl_sync(0xffffffffu, e, __ffs(found) - 1) & 0x3FFFFFull);
   } else {
+    // not in its first bucket: allocate only if some voxel is updated
+    bool any = false;
+#pragma unroll 2
+    for (int j = 0; j < 16; ++j) {
+      const int h = j & 1, z = j >> 1;
+      float x;
+      int dec = decide_fast(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, h, z, (float)z, x);
+      if (dec == kAmbiguous)
+        dec = decide_exact(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, lane & 7, (lane >> 3) + 4 * h, z, x);
+      any |= dec != -1;
+    }
+    if (!__any_sync(0xffffffffu, any)) return;
     int pl = -1, nw = 0;
     if (lane == 0) {
       bool is_new;
@@ -457,72 +561,101 @@ __device__ __forceinline__ void integrate_block(const DevVol& v, const DevFrame&
     }
     pool = __shfl_sync(0xffffffffu, pl, 0);
     fresh = __shfl_sync(0xffffffffu, nw, 0) != 0;
+    if (pool < 0) return;
   }
-  if (pool < 0) return;
   my_new += (lane == 0 && fresh) ? 1u : 0u;
-  my_updated += __popc(passbits);
-  if constexpr (ST == RF_STORAGE_FP32) {
-    uint2* vb = v.vox + (size_t)pool * kBV + lane;
-    uint8_t* wb = v.W + (size_t)pool * kBV + lane;
-    // 4) read-modify-write
-#pragma unroll 4
-    for (int j = 0; j < kVPL; ++j) {
-      const bool pass = (passbits >> j) & 1u;
-      uint2 w;
-      unsigned W;
-      if (fresh) {
-        w = make_uint2(nan_bits, 0u);
-        W = 0;
-      } else {
-        if (!pass) continue;
-        w = vb[32 * j];
-        W = wb[32 * j];
-      }
-      if (pass) {
-        const float F = __uint_as_float(w.x);
-        const float x = sx[j][lane];
-        const int px = spx[j][lane];
-        const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
-        w.x = __float_as_uint(Fn);
-        if (px < 0) w.y = colour_update(w.y, f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);  // band
-        W = min(W + 1, (unsigned)p.w_max);
-      }
-      vb[32 * j] = w;
-      wb[32 * j] = (uint8_t)W;
+  int n_amb = 0;  // voxels queued for the exact path (warp-uniform count)
+  // main pass: four voxels at a time (pixel decisions, then loads, then stores)
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    const int h = g & 1, z0 = (g >> 1) * 4;
+    const float z0f = (g >> 1) ? 4.0f : 0.0f;
+    int dec[4];
+    float xv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      dec[k] = decide_fast(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, h, z0 + k, z0f + (float)k, xv[k]);
+      const bool amb = dec[k] == kAmbiguous;
+      const unsigned m = __ballot_sync(0xffffffffu, amb);
+      if (amb) aq[n_amb + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(lane + 32 * h + 64 * (z0 + k));
+      n_amb += __popc(m);
+      my_updated += dec[k] >= 0 || dec[k] < -2 ? 1u : 0u;  // pixel index, band bit or not
     }
-  } else {
-    // FP16 storage: the tracking word always, the colour word inside the band
-    unsigned* tb = trk_words_rw(v, pool) + lane;
-    unsigned* cb = tb + kBV;
-#pragma unroll 4
-    for (int j = 0; j < kVPL; ++j) {
-      const bool pass = (passbits >> j) & 1u;
-      unsigned t;
-      if (fresh) {
-        t = kTrkEmpty;
-      } else {
-        if (!pass) continue;
-        t = tb[32 * j];
-      }
-      unsigned col = 0u;
-      bool col_written = fresh;
-      if (pass) {
-        const unsigned W = t >> 24;
-        const float x = sx[j][lane];
-        const int px = spx[j][lane];
-        const float F = __half2float(__ushort_as_half((unsigned short)(t & 0xFFFFu))) * p.tau;
-        const float Fn = (W == 0) ? x : __fdividef((float)W * F + x, (float)(W + 1));
-        const unsigned h = (unsigned)__half_as_ushort(__float2half_rn(Fn * p.inv_tau));
-        unsigned i8 = (t >> 16) & 255u;
-        if (px < 0) {  // band: colour, and the intensity derived from it
-          col = colour_update(fresh ? 0u : cb[32 * j], f.rgb + 3 * (size_t)(px & 0x7fffffff), p.w_max);
-          col_written = true;
-          i8 = rgb_i8(col);
+    if constexpr (ST == RF_STORAGE_FP32) {
+      uint2* vb = v.vox + (size_t)pool * kBV + lane + 32 * h;
+      uint8_t* wb = v.W + (size_t)pool * kBV + lane + 32 * h;
+      uint2 w[4];
+      unsigned W[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool upd = dec[k] >= 0 || dec[k] < -2;
+        w[k] = make_uint2(0x7fc00000u, 0u);
+        W[k] = 0u;
+        if (upd && !fresh) {
+          w[k] = vb[64 * (z0 + k)];
+          W[k] = wb[64 * (z0 + k)];
         }
-        t = h | (i8 << 16) | (min(W + 1, (unsigned)p.w_max) << 24);
       }
-      tb[32 * j] = t;
-      if (col_written) cb[32 * j] = col;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool upd = dec[k] >= 0 || dec[k] < -2;
+        if (upd) update_fp32(w[k], W[k], dec[k], xv[k], sh, f.rgb, p.w_max);
+        if (upd || fresh) {
+          vb[64 * (z0 + k)] = w[k];
+          wb[64 * (z0 + k)] = (uint8_t)W[k];
+        }
+      }
+    } else {
+      unsigned* tb = trk_words_rw(v, pool) + lane + 32 * h;
+      unsigned* cb = tb + kBV;
+      unsigned t[4], col[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool upd = dec[k] >= 0 || dec[k] < -2;
+        t[k] = kTrkEmpty;
+        col[k] = 0u;
+        if (upd && !fresh) {
+          t[k] = tb[64 * (z0 + k)];
+          if (dec[k] < -2) col[k] = cb[64 * (z0 + k)];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool upd = dec[k] >= 0 || dec[k] < -2;
+        bool cw = fresh;
+        if (upd) update_fp16(t[k], col[k], cw, dec[k], xv[k], sh, f.rgb, p);
+        if (upd || fresh) tb[64 * (z0 + k)] = t[k];
+        if (cw) cb[64 * (z0 + k)] = col[k];
+      }
+    }
+  }
+  if (n_amb == 0) return;
+  __syncwarp();  // the main pass's stores (fresh blocks: every voxel) are visible to the warp
+  for (int q0 = 0; q0 < n_amb; q0 += 32) {
+    const int q = q0 + lane;
+    if (q >= n_amb) break;
+    const int j = aq[q];
+    const int vx = j & 7, vy = (j >> 3) & 7, vz = j >> 6;
+    float x;
+    const int dec = decide_exact(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, vx, vy, vz, x);
+    if (dec == -1) continue;
+    my_updated += 1u;
+    if constexpr (ST == RF_STORAGE_FP32) {
+      uint2* wp = v.vox + (size_t)pool * kBV + j;
+      uint8_t* Wp = v.W + (size_t)pool * kBV + j;
+      uint2 w = *wp;
+      unsigned W = *Wp;
+      update_fp32(w, W, dec, x, sh, f.rgb, p.w_max);
+      *wp = w;
+      *Wp = (uint8_t)W;
+    } else {
+      unsigned* tp = trk_words_rw(v, pool) + j;
+      unsigned t = *tp;
+      unsigned col = dec < 0 ? tp[kBV] : 0u;
+      bool cw = false;
+      update_fp16(t, col, cw, dec, x, sh, f.rgb, p);
+      *tp = t;
+      if (cw) tp[kBV] = col;
     }
   }
 }
@@ -535,28 +668,43 @@ __device__ __forceinline__ void integ_flush(IntegState* st, unsigned updated, un
   if (lane == 0 && fresh) atomicAdd(&st->new_blocks, (int)fresh);
 }
 
-// One warp per candidate block (static round-robin over all warps): no CTA
-// barriers.
+// Per-voxel update: one warp per candidate block (static round-robin over all
+// warps, no CTA barriers inside the loop).  Per block: the origin's exact
+// camera coordinates (int64), then per voxel only 32-bit integer and FP32
+// work: camera z exact from split 2^20 multiples and remainders, the pixel
+// from a float estimate (the exact int64 path runs after the main pass for
+// the ~2 % of voxels whose estimate lies near a rounding boundary), one load
+// of the masked depth, the exact sdf tests, then the read-modify-write of the
+// updated voxels four at a time.
 template <int ST>
-__global__ void __launch_bounds__(kIntegThreads) k_integrate(DevVol v, DevFrame f, DevParams p,
-                                                             const uint8_t* __restrict__ mask, IntegState* st,
+__global__ void __launch_bounds__(kIntegThreads, 8) k_integrate(DevVol v, DevFrame f, DevParams p,
+                                                             const uint16_t* __restrict__ dm, IntegState* st,
                                                              const int4* __restrict__ cand, long long max_cand) {
-  __shared__ int s_px[kIntegWarps][kVPL][32];    // pixel index | band << 31, or -1
-  __shared__ float s_x[kIntegWarps][kVPL][32];   // update value
-  __shared__ long long A[9], tq[3];              // quantised pose
+  __shared__ IntegShared sh;
+  __shared__ unsigned short s_aq[kIntegWarps][kBV];  // voxels queued for the exact path
+  __shared__ LaneConsts s_lc[kIntegThreads];
+  __shared__ long long s_S[kIntegWarps][4];
   if (gated_off(f.gate, kModeFirst)) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x < 9) A[threadIdx.x] = st->A[threadIdx.x];
-  if (threadIdx.x < 3) tq[threadIdx.x] = st->tq[threadIdx.x];
+  if (threadIdx.x < 9) sh.A[threadIdx.x] = st->A[threadIdx.x];
+  if (threadIdx.x < 3) {
+    sh.tq[threadIdx.x] = st->tq[threadIdx.x];
+    sh.szf[threadIdx.x] = st->szf[threadIdx.x];
+  }
+  if (threadIdx.x < 8) {
+    sh.qz[threadIdx.x] = st->qz[threadIdx.x];
+    sh.rz[threadIdx.x] = st->rz[threadIdx.x];
+  }
+  for (int w = threadIdx.x; w < 256; w += kIntegThreads) sh.rcpw[w] = 1.0f / (float)(w + 1);
   __syncthreads();
   const long long n_cand = min((long long)*(volatile int*)&st->n_cand, max_cand);
-  IntegConsts c;
-  integ_consts(A, f, p, lane, c);
+  lane_consts(sh, p.v_um, lane, s_lc[threadIdx.x]);
   const long long warp0 = ((long long)blockIdx.x * kIntegThreads + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * kIntegThreads) >> 5;
   unsigned my_updated = 0, my_new = 0;
   for (long long ci = warp0; ci < n_cand; ci += nwarps)
-    integrate_block<ST>(v, f, p, mask, A, tq, c, cand[ci], lane, s_px[wid], s_x[wid], my_updated, my_new);
+    integrate_block<ST>(v, f, p, dm, sh, s_lc[threadIdx.x], cand[ci], lane, s_aq[wid], s_S[wid], my_updated,
+                        my_new);
   integ_flush(st, my_updated, my_new, lane);
 }
 
@@ -599,8 +747,9 @@ rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream
 // The frustum search of an integration: prep, tile maxima, AABB, cull.
 static rf_status launch_frustum(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st) {
   const int tiles_x = (f.W + kTile - 1) / kTile, tiles_y = (f.H + kTile - 1) / kTile;
-  k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks, f.gate);
-  k_tilemax<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x);
+  k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks, vol->dp, f.gate);
+  k_tilemax<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x,
+                                               vol->d_dmask);
   k_integ_aabb<<<1, 32, 0, st>>>(T, f, vol->dp, vol->d_integ);
   k_cull<<<vol->sm_count * vol->launch.cull_ctas_per_sm, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
                                             vol->p.max_candidates, vol->d_status);
@@ -612,10 +761,10 @@ rf_status launch_integrate(rf_volume* vol, const DevFrame& f, const double* T, c
   if (s != RF_OK) return s;
   prof_record(vol, EV_KERNEL0, st);
   if (vol->p.storage == RF_STORAGE_FP16)
-    k_integrate<RF_STORAGE_FP16><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
+    k_integrate<RF_STORAGE_FP16><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, vol->d_dmask, vol->d_integ,
                                                                              vol->d_cand, vol->p.max_candidates);
   else
-    k_integrate<RF_STORAGE_FP32><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, mask, vol->d_integ,
+    k_integrate<RF_STORAGE_FP32><<<vol->sm_count * vol->launch.integrate_ctas_per_sm, kIntegThreads, 0, st>>>(vol->dv, f, vol->dp, vol->d_dmask, vol->d_integ,
                                                                              vol->d_cand, vol->p.max_candidates);
   prof_record(vol, EV_KERNEL1, st);
   s = check_cuda(vol, cudaGetLastError(), "integrate launch");

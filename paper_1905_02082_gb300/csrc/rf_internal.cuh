@@ -67,6 +67,7 @@ struct DevParams {
   long long theta_ppm;
   int storage;    // voxel storage mode (0: FP32, 1: compact FP16)
   float inv_tau;  // 1 / tau (FP16 encoding of F / tau)
+  unsigned du_tick;  // ticks (2^-10 um) per raw depth unit
 };
 
 // One frame in device memory plus its intrinsics in the three forms used:
@@ -142,6 +143,11 @@ struct IntegState {
   int new_blocks;
   int pool_before;  // pool size when the integration started (new blocks follow it)
   unsigned long long updated;
+  // constants of the per-voxel loop: one voxel step along world z, as a float
+  // estimate in ticks (szf) and, for the camera z coordinate, split exactly
+  // into 2^20 multiples and remainders for z = 0..7 (qz, rz)
+  float szf[3];
+  int qz[8], rz[8];
 };
 
 // Everything one stream's residual seeds, erosion and dilation need.

@@ -176,199 +176,198 @@ __device__ __forceinline__ float d2f_approx(double d, bool* ok) {
   return __uint_as_float((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xFFFFFu) << 3));
 }
 
-// d > 0 and finite (no FP64 instruction): the bit pattern of a positive
-// finite double lies strictly between those of +0 and +infinity.
-__device__ __forceinline__ bool pos_finite(double d) {
-  const long long b = __double_as_longlong(d);
-  return b > 0ll && b < 0x7FF0000000000000ll;
-}
-
 // For non-negative doubles the bit patterns order like the values.
 __device__ __forceinline__ bool nonneg_less(double a, double b) {
   return __double_as_longlong(a) < __double_as_longlong(b);
 }
 
-// FP64 reciprocal: FP32 seed refined by two FP64 Newton steps (relative
-// error ~(2^-20)^4, i.e. full double precision), far cheaper than a double
-// division on GB300's FP64 pipe.
-__device__ __forceinline__ double rcp_d(double d) {
-  bool ok;
-  const float df = d2f_approx(d, &ok);
-  if (!ok) return 1.0 / d;
-  double r = f2d_exact(__frcp_rn(df));
-  r = fma(fma(-d, r, 1.0), r, r);
-  r = fma(fma(-d, r, 1.0), r, r);
-  return r;
-}
-
-// LM state of one registration, one copy in the shared memory of every CTA,
-// plus the scratch of the warp-cooperative FP64 step.
+// LM state of one registration, one copy in the shared memory of every CTA.
 struct LMShared {
   double T[16];   // accepted pose
   double Tc[16];  // candidate pose under evaluation
-  double H[21], g[6], E;
-  double lambda, fin_E;
-  double red[29];
-  // scratch of the damped 6x6 solve and of the exponential map
-  double A6[36], adjP[9], Pi[9], X[12], Y[12], adjS[9], d[6], coef[3], Ex[12];
+  double E, lambda, fin_E;
   long long N, fin_N;
-  float redf[29];  // FP32 sums of the partials
-  float Rf[12];    // float copy of T  (R row-major, then t)
-  float Rcf[12];   // float copy of Tc
-  int done, accept, solve_ok;
+  float Hf[21], gf[6];  // normal equations of the accepted pose (FP32 sums, exact in FP64)
+  float redf[29];       // FP32 sums of the partials of the evaluation just reduced
+  float Rf[12];         // float copy of T  (R row-major, then t)
+  float Rcf[12];        // float copy of Tc
+  int done;
   rf_track_info info;
 };
 
-// (row, column) of the 21 upper-triangle entries of H, row-major
-__constant__ unsigned char kUpperRow[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
-__constant__ unsigned char kUpperCol[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
-// Taylor coefficients in th^2 of A = sin(th)/th, B = (1 - cos th)/th^2 and
-// C = (th - sin th)/th^3, highest power first (th^10 ... th^0)
-__constant__ double kExpCoef[3][6] = {
-    {-1.0 / 39916800.0, 1.0 / 362880.0, -1.0 / 5040.0, 1.0 / 120.0, -1.0 / 6.0, 1.0},
-    {-1.0 / 479001600.0, 1.0 / 3628800.0, -1.0 / 40320.0, 1.0 / 720.0, -1.0 / 24.0, 0.5},
-    {-1.0 / 6227020800.0, 1.0 / 39916800.0, -1.0 / 362880.0, 1.0 / 5040.0, -1.0 / 120.0, 1.0 / 6.0}};
+// Packed index of entry (i, j), i <= j, of the upper triangle of a symmetric
+// 6x6 matrix (row-major: the order of the 21 sums of J^T J).
+__host__ __device__ constexpr int up6(int i, int j) { return i * 6 - i * (i - 1) / 2 + (j - i); }
+// Packed index of entry (i, j), j <= i, of a lower-triangular 6x6 matrix.
+__host__ __device__ constexpr int lo6(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// Cofactor (r, c) of a row-major 3x3 matrix; the adjugate is its transpose.
-__device__ __forceinline__ double cofactor3(const double* a, int r, int c) {
-  const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-  return fma(a[r1 * 3 + c1], a[r2 * 3 + c2], -a[r1 * 3 + c2] * a[r2 * 3 + c1]);
-}
-
-// One LM step, executed by the 32 lanes of one warp.  On GB300 every FP64
-// warp instruction costs the FP64 pipe about the same whatever the number of
-// active lanes, so the work is spread across lanes and the number of FP64
-// instructions on the critical path is kept small (about 70).
-//   mode 0: first evaluation of a level, at T (always taken);
-//   mode 1: evaluation of the candidate Tc, accepted when the mean cost
-//           decreases (En/Nn < E/N, compared as En N < E Nn).
-// Solve of (H + lambda diag H) d = -g in FP64 by 3x3 block elimination over
-// the translation / rotation blocks, A = [P Q; Q^T S]:
-//   P^-1 = adj(P)/det P,  [M | y1] = P^-1 [Q | b1],
-//   [Sc | r2] = [S | b2] - Q^T [M | y1]  (Schur complement),
-//   d2 = adj(Sc) r2 / det Sc,  d1 = y1 - M d2,  with b = -g.
-// Then the next candidate Tc = exp(d) T (FP64), with the se(3) exponential
-// R = I + A K + B K^2, t = (I + B K + C K^2) rho, K = [phi]x, K^2 = phi phi^T - th^2 I.
-__device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const LMConst& c, int lane) {
-  if (lane < 29) S.red[lane] = f2d_exact(S.redf[lane]);
-  __syncwarp();
-  if (lane == 0) {
-    const double En = S.red[27];
-    const long long Nn = (long long)(S.redf[28] + 0.5f);
-    S.info.evals++;
-    S.info.level_evals[level]++;
-    S.solve_ok = 1;
-    if (mode == 0) {
-      S.accept = 1;
-      S.E = En;
-      S.N = Nn;
-      S.fin_E = En;
-      S.fin_N = Nn;
-      S.done = Nn < c.min_valid ? 1 : 0;
-      S.lambda = c.lambda0;
-    } else if (Nn >= c.min_valid && En * f2d_exact((float)S.N) < S.E * f2d_exact((float)Nn)) {  // N < 2^24: exact
-      S.accept = 2;
-      S.E = En;
-      S.N = Nn;
-      S.fin_E = En;
-      S.fin_N = Nn;
-      S.lambda *= 0.1;
-    } else {
-      S.accept = 0;
-      S.lambda *= 10.0;
+// FP32 Cholesky factor A = L L^T of the damped matrix (H + lambda diag H), A
+// given by its upper triangle; inv[j] = 1 / L[j][j].  False unless every pivot
+// is positive and finite.  Fully unrolled: everything stays in registers.
+__device__ __forceinline__ bool chol6(const float A[21], float L[21], float inv[6]) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float s = A[up6(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s = fmaf(-L[lo6(j, k)], L[lo6(j, k)], s);
+    ok = ok && (s > 0.0f) && (s < 3.0e38f);
+    const float d = sqrtf(fmaxf(s, 1.0e-30f));
+    L[lo6(j, j)] = d;
+    inv[j] = 1.0f / d;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      float t = A[up6(j, i)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t = fmaf(-L[lo6(i, k)], L[lo6(j, k)], t);
+      L[lo6(i, j)] = t * inv[j];
     }
   }
-  __syncwarp();
-  const int acc = S.accept;
-  if (acc) {
-    if (lane < 21) S.H[lane] = S.red[lane];
-    else if (lane < 27) S.g[lane - 21] = S.red[lane];
-    if (acc == 2) {
+  return ok;
+}
+
+// Solves L L^T x = b with the factor of chol6 (FP32).
+__device__ __forceinline__ void chol6_solve(const float L[21], const float inv[6], const float b[6], float x[6]) {
+  float y[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float t = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) t = fmaf(-L[lo6(i, k)], y[k], t);
+    y[i] = t * inv[i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    float t = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; ++k) t = fmaf(-L[lo6(k, i)], x[k], t);
+    x[i] = t * inv[i];
+  }
+}
+
+// FP64 shuffle of a double held by lane `src` (two 32-bit shuffles).
+__device__ __forceinline__ double shfl_d(double v, int src) {
+  const long long b = __double_as_longlong(v);
+  const int lo = __shfl_sync(0xffffffffu, (int)(b & 0xffffffffll), src);
+  const int hi = __shfl_sync(0xffffffffu, (int)(b >> 32), src);
+  return __longlong_as_double(((long long)hi << 32) | (unsigned)lo);
+}
+
+// One LM step, executed by the 32 lanes of one warp.  GB300's FP64 pipe is
+// thin (an FP64 warp instruction costs tens of cycles whatever the number of
+// active lanes), so the step keeps FP64 to the solve and the pose composition
+// and issues about 18 FP64 instructions, each over parallel lanes:
+//   mode 0: first evaluation of a level, at T (always taken);
+//   mode 1: evaluation of the candidate Tc, accepted when the mean cost
+//           decreases (En/Nn < E/N, compared exactly as En N < E Nn).
+// Solve of (H + lambda diag H) d = -g: FP32 Cholesky on every lane, then one
+// step of iterative refinement with the residual -g - A d formed in FP64
+// (lanes 0-5, one row each), which gives the FP64 solution of the FP64 system
+// to within its conditioning (measured on the static room's systems: one step
+// leaves at most 3e-13 relative error).  The step's exponential map exp(d) - I
+// = [A K + B K^2 | rho + B K rho + C K^2 rho], K = [phi]x, is formed in FP32
+// (its entries are of the order of the step, so FP32 is relative to the step),
+// and the candidate Tc = T + (exp(d) - I) T is composed in FP64.
+__device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const LMConst& c, int lane) {
+  const float Enf = S.redf[27];
+  const long long Nn = (long long)(S.redf[28] + 0.5f);
+  // acceptance products and both lambda updates in one FP64 instruction
+  double prod = 0.0;
+  if (lane < 4) {
+    const double a = lane == 0 ? f2d_exact(Enf) : (lane == 1 ? S.E : S.lambda);
+    const double b = lane == 0 ? f2d_exact((float)S.N) : (lane == 1 ? f2d_exact((float)Nn) : (lane == 2 ? 0.1 : 10.0));
+    prod = a * b;
+  }
+  const double lhs = shfl_d(prod, 0), rhs = shfl_d(prod, 1), lam_dn = shfl_d(prod, 2), lam_up = shfl_d(prod, 3);
+  int accept;
+  double lambda;
+  bool done = false;
+  if (mode == 0) {
+    accept = 1;
+    lambda = c.lambda0;
+    done = Nn < c.min_valid;
+  } else if (Nn >= c.min_valid && nonneg_less(lhs, rhs)) {  // N < 2^24: both products exact
+    accept = 2;
+    lambda = lam_dn;
+  } else {
+    accept = 0;
+    lambda = lam_up;
+  }
+  if (lane == 0) {
+    S.info.evals++;
+    S.info.level_evals[level]++;
+    S.lambda = lambda;
+    if (accept) {
+      S.E = f2d_exact(Enf);
+      S.N = Nn;
+      S.fin_E = S.E;
+      S.fin_N = Nn;
+    }
+    if (mode == 0) S.done = done ? 1 : 0;  // every level starts undone unless it has too few pixels
+  }
+  if (accept) {
+    if (lane < 21) S.Hf[lane] = S.redf[lane];
+    else if (lane < 27) S.gf[lane - 21] = S.redf[lane];
+    if (accept == 2) {
       if (lane < 16) S.T[lane] = S.Tc[lane];
       if (lane < 12) S.Rf[lane] = S.Rcf[lane];
     }
   }
   __syncwarp();
-  if (S.done || last) return;
-  // damped matrix
-  if (lane < 21) {
-    const int i = kUpperRow[lane], j = kUpperCol[lane];
-    const double h = i == j ? S.H[lane] * (1.0 + S.lambda) : S.H[lane];
-    S.A6[i * 6 + j] = h;
-    S.A6[j * 6 + i] = h;
+  if (done || last) return;  // (a candidate is only evaluated while the level is not done)
+  // FP32 Cholesky of the damped matrix and first solution (every lane)
+  bool lam_ok;
+  const float lamf = d2f_approx(lambda, &lam_ok);
+  float A[21], L[21], inv[6], mg[6], d32[6], cor[6];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) A[k] = S.Hf[k];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    A[up6(i, i)] = fmaf(A[up6(i, i)], lam_ok ? lamf : 0.0f, A[up6(i, i)]);
+    mg[i] = -S.gf[i];
   }
-  __syncwarp();
-  const double* A6 = S.A6;
-  // P^-1
-  if (lane < 9) {
-    double P[9];
+  bool ok = chol6(A, L, inv) && lam_ok;
+  chol6_solve(L, inv, mg, d32);
+  // FP64 residual of row `lane` (lanes 0-5): -g_i - sum_j A_ij d_j, A in FP64
+  double r = 0.0;
+  if (lane < 6) {
+    const int i = lane;
+    r = f2d_exact(mg[0]);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) P[k] = A6[(k / 3) * 6 + (k % 3)];
-    S.adjP[lane] = cofactor3(P, lane % 3, lane / 3);
-  }
-  __syncwarp();
-  const double detP = fma(A6[0], S.adjP[0], fma(A6[1], S.adjP[3], A6[2] * S.adjP[6]));
-  if (!pos_finite(detP) || !pos_finite(A6[0])) {
-    if (lane == 0) S.solve_ok = 0;
-  } else {
-    const double rP = rcp_d(detP);
-    if (lane < 9) S.Pi[lane] = S.adjP[lane] * rP;
-    __syncwarp();
-    // [M | y1] = P^-1 [Q | b1]
-    if (lane < 12) {
-      const int r = lane >> 2, cc = lane & 3;
-      double v = 0.0;
+    for (int k = 1; k < 6; ++k) r = i == k ? f2d_exact(mg[k]) : r;  // -g_i (lane-selected)
+    const float hi = S.Hf[up6(i, i)];
+    const double hd = f2d_exact(hi);
+    const double aii = fma(hd, lambda, hd);  // H_ii (1 + lambda) in FP64
 #pragma unroll
-      for (int k = 0; k < 3; ++k) v = fma(S.Pi[r * 3 + k], cc < 3 ? A6[k * 6 + 3 + cc] : -S.g[k], v);
-      S.X[lane] = v;
-    }
-    __syncwarp();
-    // [Sc | r2] = [S | b2] - Q^T [M | y1]
-    if (lane < 12) {
-      const int r = lane >> 2, cc = lane & 3;
-      double v = cc < 3 ? A6[(3 + r) * 6 + 3 + cc] : -S.g[3 + r];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) v = fma(-A6[k * 6 + 3 + r], S.X[k * 4 + cc], v);
-      S.Y[lane] = v;
-    }
-    __syncwarp();
-    if (lane < 9) {
-      double Sc[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Sc[k] = S.Y[(k / 3) * 4 + (k % 3)];
-      S.adjS[lane] = cofactor3(Sc, lane % 3, lane / 3);
-    }
-    __syncwarp();
-    const double detS = fma(S.Y[0], S.adjS[0], fma(S.Y[1], S.adjS[3], S.Y[2] * S.adjS[6]));
-    if (!pos_finite(detS) || !pos_finite(S.Y[0])) {
-      if (lane == 0) S.solve_ok = 0;
-    } else {
-      const double rS = rcp_d(detS);
-      if (lane < 3) {
-        double v = 0.0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) v = fma(S.adjS[lane * 3 + k], S.Y[k * 4 + 3], v);
-        S.d[3 + lane] = v * rS;
-      }
-      __syncwarp();
-      if (lane < 3) {
-        double v = S.X[lane * 4 + 3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) v = fma(-S.X[lane * 4 + k], S.d[3 + k], v);
-        S.d[lane] = v;
-      }
+    for (int k = 0; k < 6; ++k) {
+      const int u = i <= k ? up6(i, k) : up6(k, i);
+      const double a = i == k ? aii : f2d_exact(S.Hf[u]);
+      r = fma(-a, f2d_exact(d32[k]), r);
     }
   }
-  __syncwarp();
-  const double d0 = S.d[0], d1 = S.d[1], d2 = S.d[2], w0 = S.d[3], w1 = S.d[4], w2 = S.d[5];
-  // |rho|^2 on even lanes and |phi|^2 on odd lanes in one pass, then exchanged
-  const int o = (lane & 1) * 3;
-  const double sq = fma(S.d[o], S.d[o], fma(S.d[o + 1], S.d[o + 1], S.d[o + 2] * S.d[o + 2]));
-  const double sq_other = __shfl_xor_sync(0xffffffffu, sq, 1);
-  const double nr2 = (lane & 1) ? sq_other : sq;
-  const double th2 = (lane & 1) ? sq : sq_other;
+  bool rok;
+  const float r32 = d2f_approx(r, &rok);
+  float rr[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) rr[k] = __shfl_sync(0xffffffffu, (rok || r == 0.0) ? r32 : 0.0f, k);
+  chol6_solve(L, inv, rr, cor);
+  // refined step in FP64 (lanes 0-5) and its squared norms (lane 0: rho, lane 1: phi)
+  double dk = 0.0;
+  if (lane < 6) {
+    float a = d32[0], b = cor[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+      a = lane == k ? d32[k] : a;
+      b = lane == k ? cor[k] : b;
+    }
+    dk = f2d_exact(a) + f2d_exact(b);
+  }
+  const double e0 = shfl_d(dk, (lane & 1) * 3), e1 = shfl_d(dk, (lane & 1) * 3 + 1), e2 = shfl_d(dk, (lane & 1) * 3 + 2);
+  const double sq = fma(e0, e0, fma(e1, e1, e2 * e2));  // lane parity selects rho or phi
+  const double nr2 = shfl_d(sq, 0), th2 = shfl_d(sq, 1);
   const double inf = __longlong_as_double(0x7FF0000000000000ll);
-  if (!S.solve_ok || !nonneg_less(nr2, inf) || !nonneg_less(th2, inf)) {
+  if (!ok || !nonneg_less(nr2, inf) || !nonneg_less(th2, inf) ||
+      (nonneg_less(nr2, c.eps_t2) && nonneg_less(th2, c.eps_r2))) {
     if (lane == 0) {
       S.info.converged[level] = 1;
       S.done = 1;
@@ -376,58 +375,49 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
     __syncwarp();
     return;
   }
-  if (nonneg_less(nr2, c.eps_t2) && nonneg_less(th2, c.eps_r2)) {
-    if (lane == 0) {
-      S.info.converged[level] = 1;
-      S.done = 1;
-    }
-    __syncwarp();
-    return;
-  }
-  // exponential map: coefficients A, B, C on lanes 0, 1, 2
-  if (lane < 3) {
-    double v;
-    if (th2 < 0.01) {
-      v = kExpCoef[lane][0];
+  // exponential map minus identity in FP32 (every lane): Er = A K + B K^2,
+  // et = rho + B K rho + C K^2 rho, with K v = phi x v
+  float dl[6];
 #pragma unroll
-      for (int k = 1; k < 6; ++k) v = fma(v, th2, kExpCoef[lane][k]);
-    } else {
-      const double th = sqrt(th2);
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      v = lane == 0 ? sn / th : (lane == 1 ? (1.0 - cs) / th2 : (th - sn) / (th2 * th));
+  for (int k = 0; k < 6; ++k) dl[k] = d32[k] + cor[k];
+  const float p0 = dl[3], p1 = dl[4], p2 = dl[5];
+  const float t2 = fmaf(p0, p0, fmaf(p1, p1, p2 * p2));
+  float cA, cB, cC;
+  if (t2 < 0.01f) {  // Taylor series in theta^2, enough terms for FP32 below theta = 0.1
+    cA = fmaf(t2, fmaf(t2, fmaf(t2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+    cB = fmaf(t2, fmaf(t2, fmaf(t2, -1.0f / 40320.0f, 1.0f / 720.0f), -1.0f / 24.0f), 0.5f);
+    cC = fmaf(t2, fmaf(t2, fmaf(t2, -1.0f / 362880.0f, 1.0f / 5040.0f), -1.0f / 120.0f), 1.0f / 6.0f);
+  } else {
+    const float th = sqrtf(t2);
+    float sn, cs;
+    sincospif(th * 0.318309886183790672f, &sn, &cs);  // argument reduction by pi is exact
+    cA = sn / th;
+    cB = (1.0f - cs) / t2;
+    cC = (th - sn) / (t2 * th);
+  }
+  const float K[9] = {0.0f, -p2, p1, p2, 0.0f, -p0, -p1, p0, 0.0f};
+  float Er[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float k2 = (i == j ? -t2 : 0.0f) + dl[3 + i] * dl[3 + j];  // K^2 = phi phi^T - theta^2 I
+      Er[i * 3 + j] = fmaf(cA, K[i * 3 + j], cB * k2);
     }
-    S.coef[lane] = v;
-  }
-  __syncwarp();
-  // R (lanes 0-8) = I + A K + B K^2 and V (lanes 9-17) = I + B K + C K^2
-  if (lane < 18) {
-    const int e = lane % 9, i = e / 3, j = e % 3;
-    const double w[3] = {w0, w1, w2};
-    const double kij = (i == j) ? 0.0 : ((j == (i + 1) % 3) ? -w[(i + 2) % 3] : w[(i + 1) % 3]);
-    const double k2ij = fma(w[i], w[j], i == j ? -th2 : 0.0);
-    const double a = lane < 9 ? S.coef[0] : S.coef[1], b = lane < 9 ? S.coef[1] : S.coef[2];
-    S.A6[lane] = fma(a, kij, fma(b, k2ij, i == j ? 1.0 : 0.0));  // scratch reuse
-  }
-  __syncwarp();
+  const float kr0 = p1 * dl[2] - p2 * dl[1], kr1 = p2 * dl[0] - p0 * dl[2], kr2 = p0 * dl[1] - p1 * dl[0];
+  const float kk0 = p1 * kr2 - p2 * kr1, kk1 = p2 * kr0 - p0 * kr2, kk2 = p0 * kr1 - p1 * kr0;
+  const float et[3] = {fmaf(cC, kk0, fmaf(cB, kr0, dl[0])), fmaf(cC, kk1, fmaf(cB, kr1, dl[1])),
+                       fmaf(cC, kk2, fmaf(cB, kr2, dl[2]))};
+  // Tc = T + [Er | et] T in FP64 (lanes 0-11: rows 0-2, columns 0-3)
   if (lane < 12) {
     const int i = lane >> 2, j = lane & 3;
-    // Ex = [R | V rho]
-    double v;
-    if (j < 3) {
-      v = S.A6[i * 3 + j];
-    } else {
-      v = fma(S.A6[9 + i * 3], d0, fma(S.A6[9 + i * 3 + 1], d1, S.A6[9 + i * 3 + 2] * d2));
-    }
-    S.Ex[lane] = v;
-  }
-  __syncwarp();
-  // Tc = Ex T  (rows 0-2; the last row stays 0 0 0 1)
-  if (lane < 12) {
-    const int i = lane >> 2, j = lane & 3;
-    double v = j == 3 ? S.Ex[i * 4 + 3] : 0.0;
+    double v = S.T[i * 4 + j];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v = fma(S.Ex[i * 4 + k], S.T[k * 4 + j], v);
+    for (int k = 0; k < 3; ++k) {  // row i of Er selected without indexing registers at run time
+      const float e = i == 0 ? Er[k] : (i == 1 ? Er[3 + k] : Er[6 + k]);
+      v = fma(f2d_exact(e), S.T[k * 4 + j], v);
+    }
+    if (j == 3) v += f2d_exact(i == 0 ? et[0] : (i == 1 ? et[1] : et[2]));
     S.Tc[lane] = v;
     S.Rcf[j < 3 ? i * 3 + j : 9 + i] = (float)v;
   }

@@ -47,6 +47,7 @@ struct rf_volume {
   // integration scratch
   rf::IntegState* d_integ = nullptr;
   int* d_tilemax = nullptr;
+  uint16_t* d_dmask = nullptr;  // per pixel: raw depth if valid and not masked, else 0
   int4* d_cand = nullptr;
 
   // whole-frame staging (graph-replayed pipeline reads only these)
