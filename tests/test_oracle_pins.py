@@ -903,3 +903,22 @@ def test_tracking_footprint_fixture_matches_the_oracle(oracle_mod):
     rows = [r for r in g["rows"] if r["frame"] == 1]
     assert [(r["blocks_probed"], r["voxels_read"]) for r in rows] == [(b1, v1), (b2, v2)]
     assert 0 < b1 < vol.num_blocks and 0 < v1 < 512 * b1
+
+
+def test_model_intensity_uses_the_papers_luminance_weights(oracle_mod):
+    """V_I of a model whose voxels all carry one colour (R, G, B) is the
+    intensity of Sec. III-B, (w_R R + w_G G + w_B B) / 255, with the weights
+    printed there (tests/golden/intensity_weights.json); the gradient is zero."""
+    O = oracle_mod
+    w = json.load(open(os.path.join(GOLDEN, "intensity_weights.json")))["weights"]
+    coords = [(bx, by, bz) for bx in range(2) for by in range(2) for bz in range(2)]
+    snap = _snapshot_from_field(coords, lambda p: p[..., 2] - 0.05, 0.02)
+    for rgb in ((255, 0, 0), (0, 255, 0), (0, 0, 255), (200, 100, 50)):
+        snap["rgb"][:] = rgb
+        snap["wc"][:] = 1
+        vol = O.OracleVolume(voxel_size=0.02)
+        vol.import_(snap)
+        ok, s, gs, I, gI, cok = vol.lookup(np.array([0.1234, 0.1711, 0.0931]))
+        assert ok and cok
+        assert abs(I - np.dot(w, rgb) / 255.0) < 1e-14, (rgb, I)
+        np.testing.assert_allclose(gI, 0.0, atol=1e-12)
