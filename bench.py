@@ -14,9 +14,8 @@ frames); runs asked for more frames than that play the 300 back and forth.
 N > 1 (under torch.distributed.run): one independent camera stream per GPU
 (weak scaling, no data-path collective); the timed region is bracketed by a
 barrier and the max over ranks is reported.
---impl reference: the FP64 CPU oracle on the host cores, each step a bounded
-sample (the centre 160x120 window of the frame, 1/16 of the pixels), scaled
-to frames/s of the full frame.
+--impl reference: the FP64 CPU oracle on one host core, each step one whole
+640x480 frame of the same workload.
 """
 from __future__ import annotations
 
@@ -40,7 +39,6 @@ METRIC = "frames/s @640x480 and % HBM roofline; p99 frame latency, 32 streams"
 CONFIG = "static"
 VOXEL, TAU, N_BUCKETS, MAX_BLOCKS = 0.01, 0.1, 1 << 20, 400_000
 L2_FLUSH_BYTES = 256 << 20
-WINDOW = (180, 300, 240, 400)  # rows, cols of the CPU sample (160x120 centre window)
 
 
 def _render(args):
@@ -109,11 +107,17 @@ def _render_clip(args):
 
 
 def render_serving_clips(plan, clip: int, workers: int):
-    jobs = [(st, clip) for st in plan]
+    """Every stream's clip, rendered in a spawn pool (before CUDA), the
+    largest frames first so that the pool stays busy."""
+    cost = {"hd": 12, "vga": 4, "qvga": 1}
+    jobs = sorted(range(len(plan)), key=lambda k: -cost[plan[k]["cam"]])
     if workers <= 1:
-        return [_render_clip(j) for j in jobs]
-    with mp.get_context("spawn").Pool(workers) as pool:
-        return pool.map(_render_clip, jobs)
+        out = {k: _render_clip((plan[k], clip)) for k in jobs}
+    else:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_render_clip, [(plan[k], clip) for k in jobs], chunksize=1)
+        out = dict(zip(jobs, res))
+    return [out[k] for k in range(len(plan))]
 
 
 def volume_size(voxel: float):
@@ -123,52 +127,82 @@ def volume_size(voxel: float):
     return blocks, buckets
 
 
-def run_serving(R, plan, clips, args):
-    """The continuous-batching serving loop against the plain per-stream path
-    on the same arrivals."""
+def _serving_specs(R, plan, clips, rate, seconds, rng, storage, bursts=None):
+    """StreamSpecs of the plan: Poisson arrivals at `rate` frames/s per stream
+    for `seconds` (bursts: per stream a list of (start, length) windows with
+    arrivals only inside them), each stream playing its clip back and forth."""
     import torch
     from synth.scenes import CAM_HD, CAM_QVGA, CAM_VGA
-    from paper_1905_02082_gb300.serving import ServingEngine, StreamSpec, pingpong, poisson_arrivals, summarize
+    from paper_1905_02082_gb300.serving import StreamSpec, pingpong, poisson_arrivals
     cams = {"qvga": CAM_QVGA, "vga": CAM_VGA, "hd": CAM_HD}
-    rng = np.random.default_rng(77)
-    n_arr = int(round(args.serving_seconds * SERVING_FPS))
     specs = []
-    for st, (frames, T0) in zip(plan, clips):
+    for k, (st, (frames, pinned, T0)) in enumerate(zip(plan, clips)):
         cam = cams[st["cam"]]
-        pinned = [(torch.from_numpy(np.ascontiguousarray(d, dtype=np.uint16)).pin_memory(),
-                   torch.from_numpy(np.ascontiguousarray(c)).pin_memory()) for d, c in frames]
+        if bursts is None:
+            arr = [t for t in poisson_arrivals(rng, int(rate * seconds * 3) + 10, rate) if t < seconds]
+        else:
+            arr = []
+            for t0, length in bursts[k]:
+                arr += [t0 + t for t in poisson_arrivals(rng, int(rate * length * 3) + 10, rate) if t < length]
         blocks, buckets = volume_size(st["voxel"])
         specs.append(StreamSpec(name=st["name"], width=cam.width, height=cam.height,
                                 K=R.Intrinsics(cam.fx, cam.fy, cam.cx, cam.cy), voxel_size=st["voxel"], frames=pinned,
-                                order=pingpong(len(frames), n_arr), arrivals=poisson_arrivals(rng, n_arr, SERVING_FPS),
-                                T0=T0, start=0.0, trunc=TAU, n_buckets=buckets, max_blocks=blocks))
-    out = {"streams": len(specs), "arrivals_per_stream": n_arr, "mean_fps_per_stream": SERVING_FPS,
-           "budget_bytes": SERVING_BUDGET,
+                                order=pingpong(len(pinned), len(arr)), arrivals=arr, T0=T0, start=0.0, trunc=TAU,
+                                n_buckets=buckets, max_blocks=blocks, storage=storage))
+    return specs
+
+
+def _serve(R, specs, budget, mode, evict_idle_s=0.25):
+    from paper_1905_02082_gb300.serving import ServingEngine, StreamSpec, summarize
+    eng = ServingEngine(budget, mode=mode, evict_idle_s=evict_idle_s)
+    # warm-up: three frames per stream, so that graph capture and first-touch costs stay out of the run
+    warm = [StreamSpec(**{**sp.__dict__, "order": sp.order[:3], "arrivals": [0.0, 0.001, 0.002]}) for sp in specs]
+    eng.run(warm, time_limit=300.0)
+    eng.results.clear()
+    eng.batch_ms.clear()
+    for k in ("evictions", "restores", "batches", "slot_reuses"):
+        eng.stats[k] = 0
+    res = eng.run(specs, time_limit=600.0)
+    summ = summarize(res)
+    summ.update({k: eng.stats[k] for k in ("evictions", "restores", "batches", "peak_bytes")})
+    summ["offered_frames"] = sum(len(sp.arrivals) for sp in specs)
+    eng.close()
+    return summ
+
+
+def run_serving(R, plan, clips, args):
+    """The continuous-batching serving loop against the plain per-stream path
+    on the same Poisson arrivals, at offered loads from 30 frames/s per stream
+    up past the GPU's capacity, and one run whose memory budget binds."""
+    import torch
+    pinned = []
+    for st, (frames, T0) in zip(plan, clips):
+        pinned.append((frames, [(torch.from_numpy(np.ascontiguousarray(d, dtype=np.uint16)).pin_memory(),
+                                 torch.from_numpy(np.ascontiguousarray(c)).pin_memory()) for d, c in frames], T0))
+    out = {"streams": len(plan), "clip_frames": args.serving_clip, "budget_bytes": SERVING_BUDGET,
            "mix": {c: sum(1 for st in plan if st["cam"] == c) for c in SERVING_CAMS},
            "workload": "32 streams, 320x240/640x480/1280x720 cycled, voxel 1-4 cm (>=2 cm at 1280x720), 0-3 movers, "
                        "Poisson arrivals; each stream plays a rendered clip back and forth; frames in page-locked "
-                       "host memory, read by the batch's staging kernel"}
-    # the batched FP16 form, the batched FP32 form, and the plain per-stream FP32 path
-    for name, mode, storage in (("batch_fp16", "batch", R.STORAGE_FP16), ("batch_fp32", "batch", R.STORAGE_FP32),
-                                ("per_stream_fp32", "per_stream", R.STORAGE_FP32)):
-        run_specs = [StreamSpec(**{**sp.__dict__, "storage": storage}) for sp in specs]
-        eng = ServingEngine(SERVING_BUDGET, mode=mode)
-        # warm-up: one short pass so that graph capture and first-touch costs stay out of the timed run
-        warm = [StreamSpec(**{**sp.__dict__, "order": sp.order[:3], "arrivals": [0.0, 0.001, 0.002]})
-                for sp in run_specs]
-        eng.run(warm, time_limit=120.0)
-        eng.results.clear()
-        eng.batch_ms.clear()
-        res = eng.run(run_specs, time_limit=300.0)
-        summ = summarize(res)
-        summ["peak_bytes"] = eng.stats["peak_bytes"]
-        summ["batches"] = eng.stats["batches"]
-        if eng.batch_ms:
-            summ["batch_call_ms"] = {"p50": float(np.percentile(eng.batch_ms, 50)),
-                                     "max": float(np.max(eng.batch_ms)),
-                                     "over_20ms": int(np.sum(np.array(eng.batch_ms) > 20.0))}
-        out[name] = summ
-        eng.close()
+                       "host memory, read by the batch's staging kernel", "loads": []}
+    for rate in args.serving_rates:
+        row = {"fps_per_stream": rate, "offered_frames_per_s": rate * len(plan)}
+        for name, mode, storage in (("batch_fp16", "batch", R.STORAGE_FP16),
+                                    ("per_stream_fp32", "per_stream", R.STORAGE_FP32)):
+            rng = np.random.default_rng(77)  # the same arrivals for both forms
+            specs = _serving_specs(R, plan, pinned, rate, args.serving_seconds, rng, storage)
+            row[name] = _serve(R, specs, SERVING_BUDGET, mode)
+        out["loads"].append(row)
+    # a budget that binds: 40 % of the streams' volumes; each stream sends two
+    # bursts (staggered), so idle streams are evicted to the host and restored
+    rng = np.random.default_rng(78)
+    bursts = [[(0.05 * k % 0.8, 0.35), (1.0 + 0.05 * k % 0.8, 0.35)] for k in range(len(plan))]
+    specs = _serving_specs(R, plan, pinned, SERVING_FPS, 0.0, rng, R.STORAGE_FP16, bursts=bursts)
+    total = sum(sp.footprint() for sp in specs)
+    budget = int(0.4 * total)
+    binding = _serve(R, specs, budget, "batch", evict_idle_s=0.1)
+    binding.update({"budget_bytes": budget, "all_volumes_bytes": total,
+                    "arrivals": "two 0.35 s Poisson bursts per stream at 30 frames/s, starts staggered by 50 ms"})
+    out["budget_binding_fp16"] = binding
     return out
 
 
@@ -211,15 +245,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-FLOPS_PER_SAMPLE = 320  # FP32 flops of one sampled pixel in one cost evaluation (depth + colour terms)
-# DRAM bytes (read + write) per launch on this workload from one ncu capture each (None once the kernel has
-# changed since its capture).  k_register: captured on the current code.  k_integrate: captured before its
-# per-voxel loop moved into a device function (same loads and stores, same 96 registers), so that figure is
-# context only.
-REGISTER_DRAM_BYTES = 6.876160e6 + 50.432e3
-INTEGRATE_DRAM_BYTES = None
-INTEGRATE_DRAM_BYTES_EARLIER = 37.697792e6 + 86.528e3
+FLOPS_PER_SAMPLE = 320  # FP32 flops of one sampled pixel and cost evaluation (hand count; the ALU estimate only)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic bytes of one registration on this workload: the distinct voxels and
+# blocks its lookups touch, plus every pixel's depth and colour (and the mask of
+# the second registration), counted by the FP64 oracle on the static room and
+# stored with the script that wrote it.
+FOOTPRINT = os.path.join(ROOT, "tests", "golden", "track_footprint_static.json")
+# DRAM bytes (read + write) per launch on this workload from one ncu capture of the
+# kernel as it stands (None once the kernel has changed since its capture).
+REGISTER_DRAM_BYTES = None
+INTEGRATE_DRAM_BYTES = None
 
 
 def rank_seed(rank: int) -> int:
@@ -250,32 +286,53 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def _oracle_frame(O, d, rgb, cam):
+    return O.FrameData(d, rgb, cam.fx, cam.fy, cam.cx, cam.cy)
+
+
+def _oracle_stream(args):
+    """One independent camera stream on the oracle (a worker process): frame 0
+    integrated at its pose, then whole frames 1..n timed; returns seconds."""
+    seed, n = args
+    from oracle import oracle as O
+    from synth import make_sequence
+    seq = make_sequence(CONFIG, seed)
+    cam = seq.camera
+    vol = O.OracleVolume(voxel_size=VOXEL, trunc=TAU)
+    d, rgb, T, _ = seq.frame(0)
+    T, _, _ = vol.process_frame(_oracle_frame(O, d, rgb, cam), T)
+    frames = [seq.frame(i)[:2] for i in range(1, n + 1)]
+    t0 = time.perf_counter()
+    for d, rgb in frames:
+        T, _, _ = vol.process_frame(_oracle_frame(O, d, rgb, cam), T)
+    return time.perf_counter() - t0
+
+
 def run_reference(args):
-    """FP64 oracle on host cores, bounded sample per step."""
+    """FP64 oracle on the host cores, one thread: every step is one whole
+    640x480 frame of the workload (track, mask, re-track, integrate)."""
     from oracle import oracle as O
     from synth import make_sequence
     n = args.warmup + args.steps
-    seq = make_sequence(CONFIG, 0, n_frames=n)
+    seq = make_sequence(CONFIG, 0)
     cam = seq.camera
-    r0, r1, c0, c1 = WINDOW
-    scale = (cam.height * cam.width) / float((r1 - r0) * (c1 - c0))
+    frames = make_frames(0, n + 1, max(1, min(16, os.cpu_count() or 1)))
     vol = O.OracleVolume(voxel_size=VOXEL, trunc=TAU)
     T = None
     times = []
-    for i in range(n):
-        d, rgb, Tgt, _ = seq.frame(i)
-        f = O.FrameData(d[r0:r1, c0:c1], rgb[r0:r1, c0:c1], cam.fx, cam.fy, cam.cx - c0, cam.cy - r0)
+    for i in range(n + 1):
+        d, rgb, Tgt = frames[i]
         t0 = time.perf_counter()
-        T, _, _ = vol.process_frame(f, Tgt if T is None else T)
+        T, _, _ = vol.process_frame(_oracle_frame(O, d, rgb, cam), Tgt if T is None else T)
         dt = time.perf_counter() - t0
-        if i >= args.warmup:
+        if i > args.warmup:  # frame 0 (integration only) and the warm-up frames untimed
             times.append(dt)
     total = sum(times)
-    fps = len(times) / (total * scale)
-    sample = (f"centre {c1 - c0}x{r1 - r0} window of each 640x480 frame (1/{scale:g} of the pixels), "
-              f"whole-frame time = window time x {scale:g}")
+    fps = len(times) / total
+    sample = (f"whole 640x480 frames {args.warmup + 1}-{n} of the static room (frame 0 integrated at its pose and "
+              f"{args.warmup} warm-up frames untimed), one thread")
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total * scale / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "static room 640x480, fx=fy=525, voxel 1 cm, tau 0.1 m", "global_batch": 1,
                        "seq_len": 1, "parallelism": "none (single-threaded CPU oracle)"},
@@ -284,36 +341,35 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def cpu_baseline(n_frames: int = 4):
-    """The oracle, as it stands, on a bounded sample of the same workload."""
+def cpu_baseline(n_frames: int = 3):
+    """The oracle, as it stands, on bounded samples of the workload: whole
+    640x480 frames on one thread; the tiny configuration in full; and all
+    host cores at once, one independent stream per core (the oracle itself is
+    sequential: streams are its only parallelism)."""
     from oracle import oracle as O
     from synth import make_sequence
-    seq = make_sequence(CONFIG, 0, n_frames=n_frames + 1)
-    cam = seq.camera
-    r0, r1, c0, c1 = WINDOW
-    scale = (cam.height * cam.width) / float((r1 - r0) * (c1 - c0))
-    vol = O.OracleVolume(voxel_size=VOXEL, trunc=TAU)
+    cores = max(1, os.cpu_count() or 1)
+    t_single = _oracle_stream((0, n_frames))
+    tiny = make_sequence("tiny", 0)
+    tcam = tiny.camera
+    tfr = [tiny.frame(i) for i in range(len(tiny))]
+    tvol = O.OracleVolume(voxel_size=0.02, trunc=TAU)
     T = None
-    total = 0.0
-    for i in range(n_frames + 1):
-        d, rgb, Tgt, _ = seq.frame(i)
-        f = O.FrameData(d[r0:r1, c0:c1], rgb[r0:r1, c0:c1], cam.fx, cam.fy, cam.cx - c0, cam.cy - r0)
-        t0 = time.perf_counter()
-        T, _, _ = vol.process_frame(f, Tgt if T is None else T)
-        if i > 0:
-            total += time.perf_counter() - t0
-    # one full-size frame as a check of the window scaling
-    vol_full = O.OracleVolume(voxel_size=VOXEL, trunc=TAU)
-    d0, rgb0, T0, _ = seq.frame(0)
-    d1, rgb1, T1, _ = seq.frame(1)
-    vol_full.process_frame(O.FrameData(d0, rgb0, cam.fx, cam.fy, cam.cx, cam.cy), T0)
     t0 = time.perf_counter()
-    vol_full.process_frame(O.FrameData(d1, rgb1, cam.fx, cam.fy, cam.cx, cam.cy), T0)
-    full = time.perf_counter() - t0
-    return {"value": n_frames / (total * scale), "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"frames 1-{n_frames} of the workload, centre {c1 - c0}x{r1 - r0} window (1/{scale:g} of "
-                      f"the pixels), time x {scale:g}; one full 640x480 frame took {full:.2f} s "
-                      f"({1.0 / full:.3f} frames/s)"}
+    for d, rgb, Tgt, _ in tfr:
+        T, _, _ = tvol.process_frame(_oracle_frame(O, d, rgb, tcam), Tgt if T is None else T)
+    t_tiny = time.perf_counter() - t0
+    with mp.get_context("spawn").Pool(cores) as pool:
+        t_all = pool.map(_oracle_stream, [(2000 + k, 1) for k in range(cores)])
+    all_fps = cores / max(t_all)
+    return {"value": n_frames / t_single, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"whole 640x480 frames 1-{n_frames} of the static room (frame 0 integrated at its pose, "
+                      f"untimed), one thread",
+            "all_cores": {"value": all_fps, "unit": "frames/s", "cores": cores,
+                          "sample": f"{cores} independent streams (one per core, distinct seeds), one whole "
+                                    f"640x480 frame each after its first; value = streams / slowest stream's time"},
+            "tiny_full": {"frames_per_s": (len(tfr) - 1) / t_tiny, "frames": len(tfr),
+                          "sample": "the tiny configuration in full (160x120, 2 cm voxels), one thread"}}
 
 
 def run_single(R, frames, K, cam, dev, stream, flush, args, storage):
@@ -347,6 +403,69 @@ def run_single(R, frames, K, cam, dev, stream, flush, args, storage):
     vol.close()
     return {"storage": "fp16" if storage else "fp32", "frames_per_s": len(ms) / (sum(ms) / 1000.0),
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}}
+
+
+def _render_precision(args):
+    i, n = args
+    from synth import make_sequence
+    return make_sequence("precision", 0, n_frames=n).frame(i)[:3]
+
+
+def run_precision(R, frames, dev, stream, flush, warmup):
+    """The precision configuration (1280x720, voxel 0.5 cm, tau 5 cm, 2^22
+    buckets) through rf_process_frame, FP16 storage and FP32 storage on the
+    same frames: frames/s and per-frame latency of each (same timing rules as
+    the headline loop), and the FP16 form's drift from the FP32 form (pose
+    difference per frame; the TSDF difference on the blocks both hold)."""
+    import torch
+    from synth.scenes import CAM_HD as cam
+    K = R.Intrinsics(cam.fx, cam.fy, cam.cx, cam.cy)
+    d_depth = [torch.from_numpy(f[0].astype(np.int32)).to(dev).to(torch.uint16).contiguous() for f in frames]
+    d_rgb = [torch.from_numpy(f[1]).to(dev).contiguous() for f in frames]
+    out = {"workload": f"precision configuration: {len(frames)} frames of 1280x720 (fx=fy=1050), voxel 0.5 cm, "
+                       "tau 5 cm, 2^22 buckets", "frames": len(frames)}
+    poses, snaps = {}, {}
+    for name, storage in (("fp16", R.STORAGE_FP16), ("fp32", R.STORAGE_FP32)):
+        vol = R.Volume(n_buckets=1 << 22, max_blocks=1_500_000, max_width=cam.width, max_height=cam.height,
+                       voxel_size=0.005, trunc=0.05, storage=storage)
+        T = torch.as_tensor(frames[0][2], device=dev).contiguous()
+        Tn = torch.empty_like(T)
+        ms, P = [], []
+        for i in range(len(frames)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            R.rf_process_frame(vol.h, vol.frame(d_depth[i], d_rgb[i], K), T, Tn, None, None, stream)
+            b.record(stream)
+            T, Tn = Tn, T
+            b.synchronize()
+            if i >= warmup:
+                ms.append(a.elapsed_time(b))
+            P.append(T.cpu().numpy())
+        vol.sync()
+        poses[name] = P
+        snaps[name] = vol.export()
+        out[name] = {"frames_per_s": len(ms) / (sum(ms) / 1000.0),
+                     "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+                     "blocks": int(len(snaps[name]["coords"]))}
+        vol.close()
+    dt = [float(np.linalg.norm(a[:3, 3] - b[:3, 3])) for a, b in zip(poses["fp16"], poses["fp32"])]
+    dr = [float(np.arccos(np.clip((np.trace(a[:3, :3] @ b[:3, :3].T) - 1) / 2, -1, 1)))
+          for a, b in zip(poses["fp16"], poses["fp32"])]
+    gt = [float(np.linalg.norm(a[:3, 3] - f[2][:3, 3])) for a, f in zip(poses["fp16"], frames)]
+    ka = {tuple(c): i for i, c in enumerate(snaps["fp16"]["coords"])}
+    kb = {tuple(c): i for i, c in enumerate(snaps["fp32"]["coords"])}
+    common = [c for c in ka if c in kb]
+    ia = np.array([ka[c] for c in common], dtype=np.int64)
+    ib = np.array([kb[c] for c in common], dtype=np.int64)
+    both = (snaps["fp16"]["W"][ia] > 0) & (snaps["fp32"]["W"][ib] > 0)
+    fd = np.abs(snaps["fp16"]["F"][ia][both].astype(np.float64) - snaps["fp32"]["F"][ib][both])
+    out["fp16_vs_fp32"] = {"pose_m_max": max(dt), "pose_m_last": dt[-1], "pose_rad_max": max(dr),
+                           "tsdf_abs_max_over_tau": float(fd.max() / 0.05) if fd.size else 0.0,
+                           "tsdf_abs_mean_over_tau": float(fd.mean() / 0.05) if fd.size else 0.0,
+                           "blocks_only_in_one": len(ka) + len(kb) - 2 * len(common),
+                           "fp16_vs_ground_truth_m_max": max(gt)}
+    return out
 
 
 def run_virtual_depth(R, frames, K, cam, dev, stream, args, n_window=10):
@@ -454,9 +573,13 @@ def main():
     ap.add_argument("--batch-streams", type=int, default=32)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--vd-frames", type=int, default=20)
+    ap.add_argument("--precision-frames", type=int, default=24)
+    ap.add_argument("--only", choices=["all", "precision"], default="all",
+                    help="precision: run only the precision section (e.g. its full 900-frame sequence)")
     ap.add_argument("--serving-streams", type=int, default=32)
-    ap.add_argument("--serving-seconds", type=float, default=2.0)
-    ap.add_argument("--serving-clip", type=int, default=3)
+    ap.add_argument("--serving-seconds", type=float, default=1.0)
+    ap.add_argument("--serving-rates", type=float, nargs="*", default=[30.0, 120.0, 360.0])
+    ap.add_argument("--serving-clip", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -468,9 +591,25 @@ def main():
             run_reference(args)
         return
 
+    workers = max(1, min(16, (os.cpu_count() or 1) // world))  # ranks share the host cores
+    pframes = []
+    if rank == 0 and args.precision_frames > 0:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pframes = pool.map(_render_precision, [(i, args.precision_frames) for i in range(args.precision_frames)],
+                               chunksize=1)
+    if args.only == "precision":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_1905_02082_gb300 import build as B
+        B.build()
+        import paper_1905_02082_gb300.refusion as R
+        dev = torch.device("cuda", local)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        prec = run_precision(R, pframes, dev, torch.cuda.current_stream(), flush, min(10, args.warmup))
+        print(json.dumps({"precision": prec}))
+        return
     n_frames = min(args.warmup + args.steps, MAX_RENDERED)
     order = frame_order(n_frames, args.warmup + args.steps)
-    workers = max(1, min(16, (os.cpu_count() or 1) // world))  # ranks share the host cores
     frames = make_frames(seed=rank_seed(rank), n=n_frames, workers=workers)
     splan = serving_plan(args.serving_streams) if args.serving_streams > 0 and rank == 0 else []
     clips = render_serving_clips(splan, args.serving_clip, workers) if splan else []
@@ -540,23 +679,57 @@ def main():
     value = job_throughput(world, args.steps, timed_ms)
 
     peak, peak_kind = measured_peaks()
-    # integration kernel (the HBM byte mover): 18 B per updated voxel, 4.5 KB per new block
+    # integration kernel (the HBM byte mover): 18 B per updated voxel (9 read, 9
+    # written), 4.5 KB per new block, plus the masked depth it reads (2 B/pixel)
     kern_ms = [p.integrate_kernel_ms for p in profs]
     upd = [p.updated_voxels for p in profs]
     newb = [p.new_blocks for p in profs]
-    bytes_per = [18 * u + 9 * 512 * nb for u, nb in zip(upd, newb)]
-    ach = (sum(bytes_per) / len(bytes_per)) / (sum(kern_ms) / len(kern_ms) / 1000.0) / 1e9
-    # registration kernel (the dominant kernel by time): FP32 algorithmic flops,
-    # FLOPS_PER_SAMPLE per sampled pixel and cost evaluation, against the
-    # CUDA-core FP32 peak (152 SMs x 128 lanes x 2 flops x 2.07 GHz)
+    npx = cam.width * cam.height
+    bytes_per = [18 * u + 9 * 512 * nb + 2 * npx for u, nb in zip(upd, newb)]
+    int_ms = sum(kern_ms) / len(kern_ms)
+    ach = (sum(bytes_per) / len(bytes_per)) / (int_ms / 1000.0) / 1e9
+    # registration kernel: its algorithmic bytes per launch (oracle-counted
+    # footprint of this workload) over the mean of both registrations' launches
+    foot = json.load(open(FOOTPRINT))
+    reg_bytes = foot["mean_bytes_fp32"]
+    reg_launch_ms = statistics.mean((pr.track_ms[0] + pr.track_ms[1]) / 2.0 for pr in profs)
+    reg_gbs = reg_bytes / (reg_launch_ms / 1000.0) / 1e9
+    # the ALU view of the same kernel (an estimate: hand-counted flops per sample)
     p = vol.params
     npix = [((cam.width + p.lm_strides[l] - 1) // p.lm_strides[l]) * ((cam.height + p.lm_strides[l] - 1) //
                                                                           p.lm_strides[l]) for l in range(3)]
     reg_ms = [pr.track_ms[1] for pr in profs]  # the second registration (its info is returned)
     reg_flops = [FLOPS_PER_SAMPLE * sum(inf.level_evals[l] * npix[l] for l in range(3)) for inf in infos]
     reg_tflops = (sum(reg_flops) / len(reg_flops)) / (sum(reg_ms) / len(reg_ms) / 1000.0) / 1e12
-    # whole frame: algorithmic bytes (inputs + integration + model read by tracking) over the frame time
-    frame_bytes = [b + cam.width * cam.height * 5 for b in bytes_per]
+    roof_reg = {"bound": "hbm", "kernel": "k_register (one registration: 3 levels, all LM evaluations)",
+                "achieved": reg_gbs, "peak": peak, "unit": "GB/s", "frac": reg_gbs / peak,
+                "traffic": REGISTER_DRAM_BYTES,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (null: the kernel "
+                                  "changed since the last capture)",
+                "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs), of " + peak_kind,
+                "bytes_per_launch": reg_bytes,
+                "bytes_source": "oracle-counted footprint: 5 B per pixel (+1 B mask) + 8 B per distinct voxel read + "
+                                "8 B per distinct block probed (tests/golden/track_footprint_static.json)",
+                "launch_ms": reg_launch_ms, "launches_per_frame": 2,
+                "note": "latency-bound: a dependent chain of LM evaluations, each a grid-wide reduction",
+                "alu_estimate": {"achieved": reg_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": reg_tflops / FP32_PEAK_TFLOPS,
+                                 "note": f"estimate: {FLOPS_PER_SAMPLE} hand-counted FP32 flops per sample; peak "
+                                         "derived as 152 SMs x 128 lanes x 2 flops x 2.07 GHz"}}
+    roof_int = {"bound": "hbm", "kernel": "k_integrate (per-voxel TSDF/colour update)",
+                "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": INTEGRATE_DRAM_BYTES,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
+                "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs), of " + peak_kind,
+                "bytes_per_launch": statistics.mean(bytes_per),
+                "bytes_source": "18 B per updated voxel + 4.5 KB per new block + 2 B per pixel of masked depth",
+                "launch_ms": int_ms, "launches_per_frame": 1}
+    # the dominant kernel by device time per frame carries the headline roofline
+    dominant = roof_reg if 2 * reg_launch_ms >= int_ms else roof_int
+    # whole frame: input once, the model reads of both registrations, the mask
+    # written, the integration's read-modify-write
+    model_reads = reg_bytes - 5 * npx - 0.5 * npx  # mean registration minus its pixel reads
+    frame_bytes = [b + 5 * npx + 2 * model_reads + npx for b in bytes_per]
     frame_gbs = (sum(frame_bytes) / len(frame_bytes)) / (statistics.mean(step_ms) / 1000.0) / 1e9
     stage = {k: statistics.mean(getattr(p, k) if k != "track_ms" else p.track_ms[0] + p.track_ms[1] for p in profs)
              for k in ("frame_ms", "track_ms", "mask_ms", "integrate_ms", "integrate_kernel_ms")}
@@ -606,6 +779,7 @@ def main():
     single_fp16 = run_single(R, frames, K, cam, dev, stream, flush, args, storage=R.STORAGE_FP16)
     virtual_depth = run_virtual_depth(R, frames, K, cam, dev, stream, args) if args.vd_frames > 0 else None
     serving = run_serving(R, splan, clips, args) if splan else None
+    precision = run_precision(R, pframes, dev, stream, flush, 4) if pframes else None
 
     if rank == 0:
         st = vol.stats()
@@ -620,22 +794,13 @@ def main():
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "mean": statistics.mean(step_ms)},
             "stages_ms": stage,
-            "roofline": {"bound": "alu", "kernel": "k_register (one registration: 3 levels, all LM evaluations)",
-                         "achieved": reg_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": reg_tflops / FP32_PEAK_TFLOPS, "traffic": REGISTER_DRAM_BYTES,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
-                         "flops_per_launch": statistics.mean(reg_flops), "launch_ms": statistics.mean(reg_ms),
-                         "note": "latency-bound: dependent LM chain with a grid barrier per evaluation"},
-            "roofline_integrate": {"bound": "hbm", "kernel": "k_integrate (per-voxel TSDF/colour update)",
-                                   "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                                   "traffic": INTEGRATE_DRAM_BYTES,
-                                   "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch; "
-                                                     f"{INTEGRATE_DRAM_BYTES_EARLIER:.4g} B before a source refactor",
-                                   "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
-                                   "bytes_per_launch": statistics.mean(bytes_per),
-                                   "launch_ms": statistics.mean(kern_ms)},
-            "frame_hbm": {"achieved": frame_gbs, "peak": peak, "unit": "GB/s", "frac": frame_gbs / peak},
+            "roofline": dominant,
+            "roofline_register": roof_reg,
+            "roofline_integrate": roof_int,
+            "frame_hbm": {"achieved": frame_gbs, "peak": peak, "unit": "GB/s", "frac": frame_gbs / peak,
+                          "bytes_per_frame": statistics.mean(frame_bytes),
+                          "bytes_source": "5 B per pixel input + both registrations' model reads + 1 B per pixel "
+                                          "mask + the integration's bytes"},
             "tracking": {"rmse_m": float(np.sqrt(np.mean(np.square(errs)))), "max_m": float(np.max(errs)),
                          "note": "free-running pose vs the ground truth of the timed frames (no loop closure)"},
             "work": {"updated_voxels": statistics.mean(upd), "new_blocks": statistics.mean(newb),
@@ -646,6 +811,7 @@ def main():
             "single_fp16": single_fp16,
             "virtual_depth": virtual_depth,
             "serving": serving,
+            "precision": precision,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_frame * args.steps,

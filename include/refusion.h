@@ -61,7 +61,7 @@ typedef enum rf_status {
  * for the quantities the paper leaves open. */
 typedef struct rf_params {
   double voxel_size;   /* metres, at most 0.15; voxel_size * 1e6 must be an integer (micrometre lattice) */
-  double trunc;        /* truncation distance tau (Sec. III-A), metres */
+  double trunc;        /* truncation distance tau (Sec. III-A), metres, below 2 */
   double w_c;          /* colour weight w_c of Eq. 4 */
   double theta;        /* flood-fill depth threshold of Alg. 1 (used as round(theta*1e6) ppm) */
   double gamma;        /* residual threshold weight of Eq. 5, t = gamma tau^2 */

@@ -100,7 +100,7 @@ rf_status validate_params(const rf_params* p) {
   if (!(p->voxel_size > 0.0 && p->voxel_size <= 0.15) || !is_integer(p->voxel_size * 1e6))
     return set_error(nullptr, RF_ERR_INVALID_ARG,
                      "voxel_size must be a positive whole number of micrometres, at most 0.15 m");
-  if (!(p->trunc > 0.0 && p->trunc < 10.0)) return set_error(nullptr, RF_ERR_INVALID_ARG, "trunc out of range");
+  if (!(p->trunc > 0.0 && p->trunc < 2.0)) return set_error(nullptr, RF_ERR_INVALID_ARG, "trunc must be in (0, 2) m");
   if (!(p->depth_scale > 0.0) || !is_integer(1e6 / p->depth_scale))
     return set_error(nullptr, RF_ERR_INVALID_ARG, "1e6/depth_scale must be an integer");
   if (!(p->d_min >= 0.0 && p->d_max > p->d_min && p->d_max <= 50.0))

@@ -52,14 +52,9 @@ __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const
     st->new_blocks = 0;
     st->updated = 0ull;
     st->pool_before = *n_blocks;
-  } else if (a < 21) {
-    // camera z of voxel step z (z = a - 13) in 2^-20 ticks, split exactly
-    const long long zs = (a - 13) * (llround(T[10] * 1073741824.0) * p.v_um);
-    st->qz[a - 13] = (int)(zs >> 20);
-    st->rz[a - 13] = (int)(zs & 0xFFFFF);
-  } else if (a < 24) {
-    // one voxel step along world z, camera coordinate i = a - 21, in ticks
-    const int i = a - 21;
+  } else if (a < 16) {
+    // one voxel step along world z, camera coordinate i = a - 13, in ticks
+    const int i = a - 13;
     st->szf[i] = (float)((double)(llround(T[8 + i] * 1073741824.0) * p.v_um) * (1.0 / 1048576.0));
   }
 }
@@ -298,17 +293,16 @@ __device__ __forceinline__ int pixel_floor(float est, float amb, bool& ambiguous
 struct IntegShared {
   long long A[9], tq[3];
   float szf[3];
-  int qz[8], rz[8];
-  float rcpw[256];  // 1 / (W + 1), W = 0..255 (running-average divisor)
+  float zlo_f, zhi_f;  // z_near and d_max in ticks (float)
+  float tau_t, du_f;   // tau and one raw depth unit in ticks (float)
+  float rcpw[256];     // 1 / (W + 1), W = 0..255 (running-average divisor)
 };
 
 // Per-lane constants: lane l owns voxels (x, y, z) = (l & 7, (l >> 3) + 4 h, z),
 // h = 0, 1, z = 0..7, i.e. block indices l + 32 h + 64 z.  Their offsets from
-// the block origin in camera coordinates: float estimates lf (ticks) and, for
-// camera z, the exact split ql * 2^20 + rl of the 2^-20-tick sum.
+// the block origin in camera coordinates, as float estimates (ticks).
 struct LaneConsts {
   float lf[3][2];
-  int ql[2], rl[2];
 };
 
 __device__ __forceinline__ void lane_consts(const IntegShared& sh, long long v_um, int lane, LaneConsts& c) {
@@ -320,10 +314,6 @@ __device__ __forceinline__ void lane_consts(const IntegShared& sh, long long v_u
     for (int i = 0; i < 3; ++i) {
       const long long L = sh.A[i * 3] * x + sh.A[i * 3 + 1] * y;
       c.lf[i][h] = ticks_f(L);
-      if (i == 2) {
-        c.ql[h] = (int)(L >> 20);
-        c.rl[h] = (int)(L & 0xFFFFF);
-      }
     }
   }
 }
@@ -333,14 +323,7 @@ struct BlockState {
   long long* S;    // exact sums, 2^-20 ticks (the warp's shared memory)
   long long Qb;    // floor(S_z / 2^20): camera z of the origin in ticks
   float base[3][2];  // float estimates of the lane's two voxel columns at z = 0
-  int rbl[2];        // remainder of S_z plus the lane's column remainder
-  int ql[2];         // the lane's column offsets: whole ticks of camera z
-  int zlo, zhi;      // z range (z_near, d_max] in ticks relative to Qb
 };
-
-__device__ __forceinline__ int clamp32(long long v) {
-  return (int)max(min(v, 2147483647ll), -2147483647ll);
-}
 
 // lc: this thread's LaneConsts (shared memory); S: the warp's 3 shared words.
 __device__ __forceinline__ void block_state(const IntegShared& sh, const DevParams& p, const LaneConsts& lc, int4 b,
@@ -359,54 +342,54 @@ __device__ __forceinline__ void block_state(const IntegShared& sh, const DevPara
   }
   bs.S = S;
   bs.Qb = s2 >> 20;
-  const int rb = (int)(s2 & 0xFFFFF);
-  bs.rbl[0] = rb + lc.rl[0];
-  bs.rbl[1] = rb + lc.rl[1];
-  bs.ql[0] = lc.ql[0];
-  bs.ql[1] = lc.ql[1];
-  bs.zlo = clamp32(p.znear_tick - bs.Qb);
-  bs.zhi = clamp32(p.dmax_tick - bs.Qb);
   __syncwarp();
 }
 
 // Update value of a voxel given its pixel's masked raw depth and its camera
 // z (Qb + dz): false when not updated (invalid or masked pixel, or occluded:
-// sdf < -tau).  sdf = D - z exactly in ticks; |sdf| <= tau: the band.
+// sdf < -tau).  sdf = D - z exactly in ticks; |sdf| <= tau: the band (tau
+// below 2 m keeps the band's sdf within 32 bits).
 __device__ __forceinline__ bool sdf_value(unsigned raw, long long Qb, int dz, const DevParams& p, float& x,
                                           bool& band) {
-  if (raw == 0u) return false;
   const long long sdf = (long long)raw * p.du_tick - Qb - dz;
-  if (sdf < -p.tau_tick) return false;
   band = sdf <= p.tau_tick;
-  x = !band ? p.tau
-            : (p.tau_tick < (1ll << 31) ? (float)(int)sdf * kTickMetres : (float)(int)(sdf >> 8) * 2.5e-7f);
-  return true;
+  x = band ? (float)(int)sdf * kTickMetres : p.tau;
+  return raw != 0u && sdf >= -p.tau_tick;
 }
 
-// Fast decision of voxel (lane, h, z): -1 when not updated, kAmbiguous when
-// the float pixel estimate is too close to a rounding boundary, else the
-// pixel index (bit 31 set inside the band) and *x the update value.
-constexpr int kAmbiguous = -2;
-__device__ __forceinline__ int decide_fast(const IntegShared& sh, const BlockState& bs, const DevFrame& f, const DevParams& p, float fxg, float fyg, float cxg,
-                                           float cyg, const uint16_t* __restrict__ dm, int h, int z, float zr,
-                                           float& x) {
-  // per-column values selected, not indexed (h is not a compile-time constant)
-  const int t = (h ? bs.rbl[1] : bs.rbl[0]) + sh.rz[z];
-  const int dz = (h ? bs.ql[1] : bs.ql[0]) + sh.qz[z] + (t >> 20);
-  if (!(dz > bs.zlo && dz <= bs.zhi)) return -1;
-  const float zf = fmaf(zr, sh.szf[2], h ? bs.base[2][1] : bs.base[2][0]);  // zr = (float)z
-  const float xf = fmaf(zr, sh.szf[0], h ? bs.base[0][1] : bs.base[0][0]);
-  const float yf = fmaf(zr, sh.szf[1], h ? bs.base[1][1] : bs.base[1][0]);
+// Fast decision of one voxel, in FP32 with error bounds and no branches: -1
+// when not updated, else the pixel index (bit 31 set inside the band) and x
+// the update value.  (bx, by, bz): float camera coordinates (ticks) of the
+// voxel's column at block z = 0; zr: its z as a float.  The camera z estimate
+// is within ez = 1e-6 z + 64 ticks of the exact one (it carries a few float
+// roundings of at most 2^-24 relative each, and the exact value is floored to
+// whole ticks), and the sdf estimate within 2 ez.  amb: a decision lies within
+// those bounds (the z range, the sdf thresholds +-tau) or the pixel estimate
+// lies too close to a rounding boundary; the voxel is then left to the exact
+// path (reported here as not updated).  Non-candidate voxels read pixel 0
+// (always in bounds) instead of branching around the load.
+__device__ __forceinline__ int decide_fast(const IntegShared& sh, const DevFrame& f, const DevParams& p, float bx,
+                                           float by, float bz, float zr, float fxg, float fyg, float cxg,
+                                           float cyg, const uint16_t* __restrict__ dm, float& x, bool& amb) {
+  const float zf = fmaf(zr, sh.szf[2], bz);
+  const float xf = fmaf(zr, sh.szf[0], bx);
+  const float yf = fmaf(zr, sh.szf[1], by);
+  const float ez = fmaf(1e-6f, fabsf(zf), 64.0f);
+  const bool zin = zf > sh.zlo_f && zf <= sh.zhi_f;
+  const bool zamb = fabsf(zf - sh.zlo_f) <= ez || fabsf(zf - sh.zhi_f) <= ez;
   const float iz = rcp_approx(zf);
   bool au, av;
   const int u = pixel_floor(fmaf(fxg * xf, iz, cxg), f.amb_u, au);
   const int v = pixel_floor(fmaf(fyg * yf, iz, cyg), f.amb_v, av);
-  if (au || av) return kAmbiguous;
-  if ((unsigned)u >= (unsigned)f.W || (unsigned)v >= (unsigned)f.H) return -1;
-  const int pix = v * f.W + u;
-  bool band = false;
-  if (!sdf_value(__ldg(dm + pix), bs.Qb, dz, p, x, band)) return -1;
-  return band ? (pix | (int)0x80000000) : pix;
+  const bool cand = zin && !(au || av) && (unsigned)u < (unsigned)f.W && (unsigned)v < (unsigned)f.H;
+  const int pix = cand ? v * f.W + u : 0;
+  const unsigned raw = __ldg(dm + pix);
+  const float sdf = fmaf(__uint_as_float(0x4B000000u | raw) - 8388608.0f, sh.du_f, -zf);  // exact float of raw
+  const bool live = cand && raw != 0u;
+  amb = zamb || (zin && (au || av)) || (live && fabsf(fabsf(sdf) - sh.tau_t) <= 2.0f * ez);
+  const bool band = sdf <= sh.tau_t;
+  x = band ? sdf * kTickMetres : p.tau;
+  return (live && sdf >= -sh.tau_t && !amb) ? (band ? (pix | (int)0x80000000) : pix) : -1;
 }
 
 // floor(num / den) for den > 0 when it lies in [0, n), else -1.  `guess` is
@@ -445,7 +428,7 @@ __device__ int decide_exact(const IntegShared& sh, const BlockState& bs, const D
   const int v = pixel_of(fyg * cf[1] * iz + cyg, f.fyq * C[1] + f.cyq * C[2], den, f.H);
   if (v < 0) return -1;
   const int pix = v * f.W + u;
-  bool band = false;
+  bool band;
   if (!sdf_value(__ldg(dm + pix), bs.Qb, (int)(C[2] - bs.Qb), p, x, band)) return -1;
   return band ? (pix | (int)0x80000000) : pix;
 }
@@ -520,6 +503,51 @@ __device__ __forceinline__ void update_fp16(unsigned& t, unsigned& col, bool& co
   t = h | (i8 << 16) | (min(W + 1u, (unsigned)p.w_max) << 24);
 }
 
+// Read-modify-write of voxel (lane, h, z0 + k) for k = 0..3 of block `pool`
+// after their decisions `dec` (-1: not updated); a fresh block gets every
+// voxel written (empty unless updated).  `o`: lane + 32 h + 64 z0.
+template <int ST>
+__device__ __forceinline__ void rmw4(const DevVol& v, const DevFrame& f, const DevParams& p, const IntegShared& sh,
+                                     int pool, bool fresh, int o, const int dec[4], const float xv[4]) {
+  if constexpr (ST == RF_STORAGE_FP32) {
+    uint2* vb = v.vox + (size_t)pool * kBV + o;
+    uint8_t* wb = v.W + (size_t)pool * kBV + o;
+    uint2 w[4];
+    unsigned W[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool ld = dec[k] != -1 && !fresh;
+      w[k] = ld ? vb[64 * k] : make_uint2(0x7fc00000u, 0u);
+      W[k] = ld ? (unsigned)wb[64 * k] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (dec[k] != -1) update_fp32(w[k], W[k], dec[k], xv[k], sh, f.rgb, p.w_max);
+      if (dec[k] != -1 || fresh) {
+        vb[64 * k] = w[k];
+        wb[64 * k] = (uint8_t)W[k];
+      }
+    }
+  } else {
+    unsigned* tb = trk_words_rw(v, pool) + o;
+    unsigned* cb = tb + kBV;
+    unsigned t[4], col[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool ld = dec[k] != -1 && !fresh;
+      t[k] = ld ? tb[64 * k] : kTrkEmpty;
+      col[k] = (ld && dec[k] < -2) ? cb[64 * k] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bool cw = fresh;
+      if (dec[k] != -1) update_fp16(t[k], col[k], cw, dec[k], xv[k], sh, f.rgb, p);
+      if (dec[k] != -1 || fresh) tb[64 * k] = t[k];
+      if (cw) cb[64 * k] = col[k];
+    }
+  }
+}
+
 // One candidate block b, integrated by one warp (see k_integrate).
 template <int ST>
 __device__ __forceinline__ void integrate_block(const DevVol& v, const DevFrame& f, const DevParams& p,
@@ -543,13 +571,14 @@ __device__ __forceinline__ void integrate_block(const DevVol& v, const DevFrame&
   } else {
     // not in its first bucket: allocate only if some voxel is updated
     bool any = false;
-#pragma unroll 2
+#pragma unroll 1
     for (int j = 0; j < 16; ++j) {
       const int h = j & 1, z = j >> 1;
       float x;
-      int dec = decide_fast(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, h, z, (float)z, x);
-      if (dec == kAmbiguous)
-        dec = decide_exact(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, lane & 7, (lane >> 3) + 4 * h, z, x);
+      bool amb;
+      int dec = decide_fast(sh, f, p, h ? bs.base[0][1] : bs.base[0][0], h ? bs.base[1][1] : bs.base[1][0],
+                            h ? bs.base[2][1] : bs.base[2][0], (float)z, fxg, fyg, cxg, cyg, dm, x, amb);
+      if (amb) dec = decide_exact(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, lane & 7, (lane >> 3) + 4 * h, z, x);
       any |= dec != -1;
     }
     if (!__any_sync(0xffffffffu, any)) return;
@@ -564,76 +593,44 @@ __device__ __forceinline__ void integrate_block(const DevVol& v, const DevFrame&
     if (pool < 0) return;
   }
   my_new += (lane == 0 && fresh) ? 1u : 0u;
-  int n_amb = 0;  // voxels queued for the exact path (warp-uniform count)
-  // main pass: four voxels at a time (pixel decisions, then loads, then stores)
+  // main pass: 16 voxels per lane, four at a time (decisions, loads, stores)
+  unsigned ambmask = 0u;  // bit 8 h + z
 #pragma unroll 1
   for (int g = 0; g < 4; ++g) {
     const int h = g & 1, z0 = (g >> 1) * 4;
+    const float bx = h ? bs.base[0][1] : bs.base[0][0], by = h ? bs.base[1][1] : bs.base[1][0];
+    const float bz = h ? bs.base[2][1] : bs.base[2][0];
     const float z0f = (g >> 1) ? 4.0f : 0.0f;
     int dec[4];
     float xv[4];
+    unsigned am = 0u;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      dec[k] = decide_fast(sh, bs, f, p, fxg, fyg, cxg, cyg, dm, h, z0 + k, z0f + (float)k, xv[k]);
-      const bool amb = dec[k] == kAmbiguous;
-      const unsigned m = __ballot_sync(0xffffffffu, amb);
-      if (amb) aq[n_amb + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(lane + 32 * h + 64 * (z0 + k));
-      n_amb += __popc(m);
-      my_updated += dec[k] >= 0 || dec[k] < -2 ? 1u : 0u;  // pixel index, band bit or not
+      bool a;
+      dec[k] = decide_fast(sh, f, p, bx, by, bz, z0f + (float)k, fxg, fyg, cxg, cyg, dm, xv[k], a);
+      am |= a ? (1u << k) : 0u;
+      my_updated += dec[k] != -1 ? 1u : 0u;
     }
-    if constexpr (ST == RF_STORAGE_FP32) {
-      uint2* vb = v.vox + (size_t)pool * kBV + lane + 32 * h;
-      uint8_t* wb = v.W + (size_t)pool * kBV + lane + 32 * h;
-      uint2 w[4];
-      unsigned W[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool upd = dec[k] >= 0 || dec[k] < -2;
-        w[k] = make_uint2(0x7fc00000u, 0u);
-        W[k] = 0u;
-        if (upd && !fresh) {
-          w[k] = vb[64 * (z0 + k)];
-          W[k] = wb[64 * (z0 + k)];
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool upd = dec[k] >= 0 || dec[k] < -2;
-        if (upd) update_fp32(w[k], W[k], dec[k], xv[k], sh, f.rgb, p.w_max);
-        if (upd || fresh) {
-          vb[64 * (z0 + k)] = w[k];
-          wb[64 * (z0 + k)] = (uint8_t)W[k];
-        }
-      }
-    } else {
-      unsigned* tb = trk_words_rw(v, pool) + lane + 32 * h;
-      unsigned* cb = tb + kBV;
-      unsigned t[4], col[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool upd = dec[k] >= 0 || dec[k] < -2;
-        t[k] = kTrkEmpty;
-        col[k] = 0u;
-        if (upd && !fresh) {
-          t[k] = tb[64 * (z0 + k)];
-          if (dec[k] < -2) col[k] = cb[64 * (z0 + k)];
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool upd = dec[k] >= 0 || dec[k] < -2;
-        bool cw = fresh;
-        if (upd) update_fp16(t[k], col[k], cw, dec[k], xv[k], sh, f.rgb, p);
-        if (upd || fresh) tb[64 * (z0 + k)] = t[k];
-        if (cw) cb[64 * (z0 + k)] = col[k];
-      }
-    }
+    ambmask |= am << (8 * h + z0);
+    rmw4<ST>(v, f, p, sh, pool, fresh, lane + 32 * h + 64 * z0, dec, xv);
   }
-  if (n_amb == 0) return;
-  __syncwarp();  // the main pass's stores (fresh blocks: every voxel) are visible to the warp
-  for (int q0 = 0; q0 < n_amb; q0 += 32) {
-    const int q = q0 + lane;
-    if (q >= n_amb) break;
+  // ambiguous voxels: queued across the warp, then one exact decision each
+  const int cnt = __popc(ambmask);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
+  int pos = incl - cnt;
+  for (unsigned m = ambmask; m; m &= m - 1u) {
+    const int bit = __ffs(m) - 1;
+    aq[pos++] = (unsigned short)(lane + 32 * (bit >> 3) + 64 * (bit & 7));
+  }
+  __syncwarp();  // the queue and the main pass's stores (fresh blocks: every voxel) are visible to the warp
+  for (int q = lane; q < total; q += 32) {
     const int j = aq[q];
     const int vx = j & 7, vy = (j >> 3) & 7, vz = j >> 6;
     float x;
@@ -658,6 +655,7 @@ __device__ __forceinline__ void integrate_block(const DevVol& v, const DevFrame&
       if (cw) tp[kBV] = col;
     }
   }
+  __syncwarp();  // the queue is reused by the warp's next block
 }
 
 // Counts of one warp for one stream's integration statistics.
@@ -670,12 +668,13 @@ __device__ __forceinline__ void integ_flush(IntegState* st, unsigned updated, un
 
 // Per-voxel update: one warp per candidate block (static round-robin over all
 // warps, no CTA barriers inside the loop).  Per block: the origin's exact
-// camera coordinates (int64), then per voxel only 32-bit integer and FP32
-// work: camera z exact from split 2^20 multiples and remainders, the pixel
-// from a float estimate (the exact int64 path runs after the main pass for
-// the ~2 % of voxels whose estimate lies near a rounding boundary), one load
-// of the masked depth, the exact sdf tests, then the read-modify-write of the
-// updated voxels four at a time.
+// camera coordinates (int64) and their float estimates; per voxel only FP32
+// work without branches: the camera coordinates, the pixel, one load of the
+// masked depth and the sdf, each decision taken in FP32 when it lies outside
+// the estimate's error bound; then the read-modify-write of the updated
+// voxels, four at a time.  The ~2 % of voxels with a decision inside an error
+// bound (almost all: a pixel estimate near a rounding boundary) are queued and
+// decided by the exact int64 path after the main pass.
 template <int ST>
 __global__ void __launch_bounds__(kIntegThreads, 8) k_integrate(DevVol v, DevFrame f, DevParams p,
                                                              const uint16_t* __restrict__ dm, IntegState* st,
@@ -691,9 +690,11 @@ __global__ void __launch_bounds__(kIntegThreads, 8) k_integrate(DevVol v, DevFra
     sh.tq[threadIdx.x] = st->tq[threadIdx.x];
     sh.szf[threadIdx.x] = st->szf[threadIdx.x];
   }
-  if (threadIdx.x < 8) {
-    sh.qz[threadIdx.x] = st->qz[threadIdx.x];
-    sh.rz[threadIdx.x] = st->rz[threadIdx.x];
+  if (threadIdx.x == 0) {
+    sh.zlo_f = (float)p.znear_tick;
+    sh.zhi_f = (float)p.dmax_tick;
+    sh.tau_t = (float)p.tau_tick;
+    sh.du_f = (float)p.du_tick;
   }
   for (int w = threadIdx.x; w < 256; w += kIntegThreads) sh.rcpw[w] = 1.0f / (float)(w + 1);
   __syncthreads();

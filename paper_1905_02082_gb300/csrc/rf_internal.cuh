@@ -98,11 +98,15 @@ __device__ __forceinline__ bool gated_off(const int* gate, int max_mode) {
   return gate != nullptr && __ldg(gate) > max_mode;
 }
 
+constexpr int kLambdaPow = 24;  // damping exponents k in [-kLambdaPow, kLambdaPow]
 struct LMConst {
   double lambda0, eps_t, eps_r;
-  double eps_t2, eps_r2;  // squared, for the convergence test
+  float eps_t2f, eps_r2f;  // squared thresholds of the convergence test
   long long min_valid;
   int iters[3], strides[3];
+  // lambda0 * 10^k rounded to float, k = -kLambdaPow .. kLambdaPow (the
+  // Marquardt damping after k more rejections than acceptances)
+  float lambda_pow[2 * kLambdaPow + 1];
 };
 
 // Everything one registration needs (one camera stream).
@@ -143,11 +147,9 @@ struct IntegState {
   int new_blocks;
   int pool_before;  // pool size when the integration started (new blocks follow it)
   unsigned long long updated;
-  // constants of the per-voxel loop: one voxel step along world z, as a float
-  // estimate in ticks (szf) and, for the camera z coordinate, split exactly
-  // into 2^20 multiples and remainders for z = 0..7 (qz, rz)
+  // constant of the per-voxel loop: one voxel step along world z in camera
+  // coordinates, as a float estimate in ticks
   float szf[3];
-  int qz[8], rz[8];
 };
 
 // Everything one stream's residual seeds, erosion and dilation need.

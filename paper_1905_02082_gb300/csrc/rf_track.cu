@@ -154,43 +154,21 @@ __device__ __forceinline__ void add_jtj(float* acc, const float J[6], float r, f
 }
 
 
-// float -> double conversions run on GB300's thin FP64 pipe; these build the
-// same values from the IEEE bit fields with integer operations.
-// Exact float -> double (normal numbers, zeros, infinities, NaN; a subnormal
-// float takes the converting instruction).
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned e = (b >> 23) & 0xFFu;
-  if (e == 0u && (b & 0x7FFFFFu) != 0u) return (double)f;
-  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
-  const unsigned long long ed = e == 0u ? 0ull : (e == 0xFFu ? 0x7FFull : (unsigned long long)(e - 127u + 1023u));
-  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
-}
-
-// A float within 2^-20 (relative) of a double whose exponent is in the
-// normal float range; flags the other cases.
-__device__ __forceinline__ float d2f_approx(double d, bool* ok) {
-  const unsigned hi = (unsigned)(__double_as_longlong(d) >> 32);
-  const int e = (int)((hi >> 20) & 0x7FFu) - 1023;
-  *ok = e > -126 && e < 127;
-  return __uint_as_float((hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xFFFFFu) << 3));
-}
-
-// For non-negative doubles the bit patterns order like the values.
-__device__ __forceinline__ bool nonneg_less(double a, double b) {
-  return __double_as_longlong(a) < __double_as_longlong(b);
-}
-
 // LM state of one registration, one copy in the shared memory of every CTA.
 struct LMShared {
-  double T[16];   // accepted pose
-  double Tc[16];  // candidate pose under evaluation
-  double E, lambda, fin_E;
+  float Ef;       // FP32 cost sum E of the accepted pose
   long long N, fin_N;
-  float Hf[21], gf[6];  // normal equations of the accepted pose (FP32 sums, exact in FP64)
+  float fin_E;
+  int lam_k;            // damping lambda0 * 10^lam_k
+  float Hf[21], gf[6];  // normal equations of the accepted pose (FP32 sums)
   float redf[29];       // FP32 sums of the partials of the evaluation just reduced
-  float Rf[12];         // float copy of T  (R row-major, then t)
-  float Rcf[12];        // float copy of Tc
+  // the accepted pose T and the candidate Tc (R row-major, then t), each
+  // entry an unevaluated sum hi + lo of two floats (about 48 bits): hi is the
+  // float pose an evaluation uses, hi + lo the pose itself
+  float Rf[12], Rlf[12];
+  float Rcf[12], Rclf[12];
+  double T0[12];  // the initial pose, returned unchanged when no candidate is accepted
+  int moved;      // some candidate was accepted
   int done;
   rf_track_info info;
 };
@@ -198,176 +176,180 @@ struct LMShared {
 // Packed index of entry (i, j), i <= j, of the upper triangle of a symmetric
 // 6x6 matrix (row-major: the order of the 21 sums of J^T J).
 __host__ __device__ constexpr int up6(int i, int j) { return i * 6 - i * (i - 1) / 2 + (j - i); }
-// Packed index of entry (i, j), j <= i, of a lower-triangular 6x6 matrix.
-__host__ __device__ constexpr int lo6(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// FP32 Cholesky factor A = L L^T of the damped matrix (H + lambda diag H), A
-// given by its upper triangle; inv[j] = 1 / L[j][j].  False unless every pivot
-// is positive and finite.  Fully unrolled: everything stays in registers.
-__device__ __forceinline__ bool chol6(const float A[21], float L[21], float inv[6]) {
+
+// FP32 Cholesky factorisation of the damped matrix in place: A holds the
+// upper triangle (row-major) on entry and L^T (L's column j stored as row j of
+// the upper triangle) on exit; inv[j] = 1 / L[j][j] from the hardware
+// reciprocal square root (the factor only preconditions the refined solve).
+// False unless every pivot is positive and finite.  Fully unrolled.
+__device__ __forceinline__ bool chol6(float A[21], float inv[6]) {
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     float s = A[up6(j, j)];
 #pragma unroll
-    for (int k = 0; k < j; ++k) s = fmaf(-L[lo6(j, k)], L[lo6(j, k)], s);
+    for (int k = 0; k < j; ++k) s = fmaf(-A[up6(k, j)], A[up6(k, j)], s);
     ok = ok && (s > 0.0f) && (s < 3.0e38f);
-    const float d = sqrtf(fmaxf(s, 1.0e-30f));
-    L[lo6(j, j)] = d;
-    inv[j] = 1.0f / d;
+    const float r = rsqrtf(fmaxf(s, 1.0e-30f));
+    A[up6(j, j)] = s * r;
+    inv[j] = r;
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {
       float t = A[up6(j, i)];
 #pragma unroll
-      for (int k = 0; k < j; ++k) t = fmaf(-L[lo6(i, k)], L[lo6(j, k)], t);
-      L[lo6(i, j)] = t * inv[j];
+      for (int k = 0; k < j; ++k) t = fmaf(-A[up6(k, i)], A[up6(k, j)], t);
+      A[up6(j, i)] = t * r;
     }
   }
   return ok;
 }
 
-// Solves L L^T x = b with the factor of chol6 (FP32).
-__device__ __forceinline__ void chol6_solve(const float L[21], const float inv[6], const float b[6], float x[6]) {
-  float y[6];
+// Solves L L^T x = b in place (b -> x) with the factor of chol6 (FP32).
+__device__ __forceinline__ void chol6_solve(const float A[21], const float inv[6], float b[6]) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     float t = b[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) t = fmaf(-L[lo6(i, k)], y[k], t);
-    y[i] = t * inv[i];
+    for (int k = 0; k < i; ++k) t = fmaf(-A[up6(k, i)], b[k], t);
+    b[i] = t * inv[i];
   }
 #pragma unroll
   for (int i = 5; i >= 0; --i) {
-    float t = y[i];
+    float t = b[i];
 #pragma unroll
-    for (int k = i + 1; k < 6; ++k) t = fmaf(-L[lo6(k, i)], x[k], t);
-    x[i] = t * inv[i];
+    for (int k = i + 1; k < 6; ++k) t = fmaf(-A[up6(i, k)], b[k], t);
+    b[i] = t * inv[i];
   }
 }
 
-// FP64 shuffle of a double held by lane `src` (two 32-bit shuffles).
-__device__ __forceinline__ double shfl_d(double v, int src) {
-  const long long b = __double_as_longlong(v);
-  const int lo = __shfl_sync(0xffffffffu, (int)(b & 0xffffffffll), src);
-  const int hi = __shfl_sync(0xffffffffu, (int)(b >> 32), src);
-  return __longlong_as_double(((long long)hi << 32) | (unsigned)lo);
+// Error-free transformations (Knuth's TwoSum, the FMA form of Dekker's
+// TwoProduct): a + b = s + e and a b = p + e exactly in FP32 arithmetic.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
 }
 
-// One LM step, executed by the 32 lanes of one warp.  GB300's FP64 pipe is
-// thin (an FP64 warp instruction costs tens of cycles whatever the number of
-// active lanes), so the step keeps FP64 to the solve and the pose composition
-// and issues about 18 FP64 instructions, each over parallel lanes:
+// a * na < b * nb, exactly, for finite floats a, b >= 0 and integers
+// 0 <= na, nb < 2^24 (each product is a 48-bit integer times a power of two).
+__device__ __forceinline__ bool prod_less(float a, unsigned na, float b, unsigned nb) {
+  const unsigned ba = __float_as_uint(a), bb = __float_as_uint(b);
+  const unsigned ea = (ba >> 23) & 255u, eb = (bb >> 23) & 255u;
+  const unsigned long long P = (unsigned long long)((ba & 0x7FFFFFu) | (ea ? 0x800000u : 0u)) * na;
+  const unsigned long long Q = (unsigned long long)((bb & 0x7FFFFFu) | (eb ? 0x800000u : 0u)) * nb;
+  if (P == 0ull || Q == 0ull) return P == 0ull && Q != 0ull;
+  const int xa = (int)(ea ? ea : 1u), xb = (int)(eb ? eb : 1u);  // exponent of the integer mantissa, + 150
+  const int ta = 63 - __clzll((long long)P) + xa, tb = 63 - __clzll((long long)Q) + xb;
+  if (ta != tb) return ta < tb;
+  return xa >= xb ? (P << (xa - xb)) < Q : P < (Q << (xb - xa));
+}
+
+// One LM step, executed by the 32 lanes of one warp.  On GB300 a dependent
+// FP64 instruction costs hundreds of cycles (measured with clock64 stamps in
+// this loop: about 300-400 per dependent FP64 operation), and the step lies
+// on the registration's serial critical path; so the step works in FP32 and
+// reaches FP64-class accuracy where it matters without FP64 latency:
 //   mode 0: first evaluation of a level, at T (always taken);
 //   mode 1: evaluation of the candidate Tc, accepted when the mean cost
-//           decreases (En/Nn < E/N, compared exactly as En N < E Nn).
-// Solve of (H + lambda diag H) d = -g: FP32 Cholesky on every lane, then one
-// step of iterative refinement with the residual -g - A d formed in FP64
-// (lanes 0-5, one row each), which gives the FP64 solution of the FP64 system
-// to within its conditioning (measured on the static room's systems: one step
-// leaves at most 3e-13 relative error).  The step's exponential map exp(d) - I
-// = [A K + B K^2 | rho + B K rho + C K^2 rho], K = [phi]x, is formed in FP32
-// (its entries are of the order of the step, so FP32 is relative to the step),
-// and the candidate Tc = T + (exp(d) - I) T is composed in FP64.
+//           decreases (En/Nn < E/N, compared exactly as En N < E Nn on the
+//           integer mantissas);
+//   damping lambda = lambda0 10^k, k counting rejections minus acceptances;
+//   solve of (H + lambda diag H) d = -g: FP32 Cholesky, then one step of
+//   iterative refinement whose residual -g - A d is formed exactly (FP32
+//   error-free transformations: the products of FP32 numbers and their sum
+//   carried to about 2^-46), which gives the solution to the accuracy of an
+//   FP64 solve for the systems met here (condition numbers ~10^2);
+//   exp(d) - I = [A K + B K^2 | rho + B K rho + C K^2 rho] in FP32 (its
+//   entries are of the order of the step, so FP32 is relative to the step);
+//   the candidate pose Tc = T + (exp(d) - I) T: the increment in FP32, the sum
+//   in FP64 (one FP64 add per entry, lanes 0-11 in parallel), and its float
+//   copy for the next evaluation.
 __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const LMConst& c, int lane) {
   const float Enf = S.redf[27];
   const long long Nn = (long long)(S.redf[28] + 0.5f);
-  // acceptance products and both lambda updates in one FP64 instruction
-  double prod = 0.0;
-  if (lane < 4) {
-    const double a = lane == 0 ? f2d_exact(Enf) : (lane == 1 ? S.E : S.lambda);
-    const double b = lane == 0 ? f2d_exact((float)S.N) : (lane == 1 ? f2d_exact((float)Nn) : (lane == 2 ? 0.1 : 10.0));
-    prod = a * b;
-  }
-  const double lhs = shfl_d(prod, 0), rhs = shfl_d(prod, 1), lam_dn = shfl_d(prod, 2), lam_up = shfl_d(prod, 3);
   int accept;
-  double lambda;
   bool done = false;
+  int k = S.lam_k;
   if (mode == 0) {
     accept = 1;
-    lambda = c.lambda0;
+    k = 0;
     done = Nn < c.min_valid;
-  } else if (Nn >= c.min_valid && nonneg_less(lhs, rhs)) {  // N < 2^24: both products exact
+  } else if (Nn >= c.min_valid && prod_less(Enf, (unsigned)S.N, S.Ef, (unsigned)Nn)) {  // N < 2^24
     accept = 2;
-    lambda = lam_dn;
+    k = max(k - 1, -kLambdaPow);
   } else {
     accept = 0;
-    lambda = lam_up;
+    k = min(k + 1, kLambdaPow);
   }
+  __syncwarp();  // every lane has read the state before lane 0 updates it
   if (lane == 0) {
     S.info.evals++;
     S.info.level_evals[level]++;
-    S.lambda = lambda;
+    S.lam_k = k;
     if (accept) {
-      S.E = f2d_exact(Enf);
+      S.Ef = Enf;
       S.N = Nn;
-      S.fin_E = S.E;
+      S.fin_E = Enf;
       S.fin_N = Nn;
     }
+    if (accept == 2) S.moved = 1;
     if (mode == 0) S.done = done ? 1 : 0;  // every level starts undone unless it has too few pixels
   }
   if (accept) {
     if (lane < 21) S.Hf[lane] = S.redf[lane];
     else if (lane < 27) S.gf[lane - 21] = S.redf[lane];
-    if (accept == 2) {
-      if (lane < 16) S.T[lane] = S.Tc[lane];
-      if (lane < 12) S.Rf[lane] = S.Rcf[lane];
+    if (accept == 2 && lane < 12) {
+      S.Rf[lane] = S.Rcf[lane];
+      S.Rlf[lane] = S.Rclf[lane];
     }
   }
   __syncwarp();
   if (done || last) return;  // (a candidate is only evaluated while the level is not done)
+  const float lam = c.lambda_pow[k + kLambdaPow];
   // FP32 Cholesky of the damped matrix and first solution (every lane)
-  bool lam_ok;
-  const float lamf = d2f_approx(lambda, &lam_ok);
-  float A[21], L[21], inv[6], mg[6], d32[6], cor[6];
+  float A[21], inv[6], d[6], r[6];
 #pragma unroll
-  for (int k = 0; k < 21; ++k) A[k] = S.Hf[k];
+  for (int q = 0; q < 21; ++q) A[q] = S.Hf[q];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    A[up6(i, i)] = fmaf(A[up6(i, i)], lam_ok ? lamf : 0.0f, A[up6(i, i)]);
-    mg[i] = -S.gf[i];
+    A[up6(i, i)] = fmaf(A[up6(i, i)], lam, A[up6(i, i)]);
+    d[i] = -S.gf[i];
   }
-  bool ok = chol6(A, L, inv) && lam_ok;
-  chol6_solve(L, inv, mg, d32);
-  // FP64 residual of row `lane` (lanes 0-5): -g_i - sum_j A_ij d_j, A in FP64
-  double r = 0.0;
-  if (lane < 6) {
-    const int i = lane;
-    r = f2d_exact(mg[0]);
+  const bool ok = chol6(A, inv);
+  chol6_solve(A, inv, d);
+  // residual -g - (H + lambda diag H) d, exact to about 2^-46 (every lane)
 #pragma unroll
-    for (int k = 1; k < 6; ++k) r = i == k ? f2d_exact(mg[k]) : r;  // -g_i (lane-selected)
-    const float hi = S.Hf[up6(i, i)];
-    const double hd = f2d_exact(hi);
-    const double aii = fma(hd, lambda, hd);  // H_ii (1 + lambda) in FP64
+  for (int i = 0; i < 6; ++i) {
+    float sh = -S.gf[i], sl = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const int u = i <= k ? up6(i, k) : up6(k, i);
-      const double a = i == k ? aii : f2d_exact(S.Hf[u]);
-      r = fma(-a, f2d_exact(d32[k]), r);
+    for (int j = 0; j < 6; ++j) {
+      const float h = S.Hf[i <= j ? up6(i, j) : up6(j, i)];
+      float p, pe, e;
+      two_prod(h, d[j], p, pe);
+      two_sum(sh, -p, sh, e);
+      sl += e - pe;
+      if (i == j) {  // the damping term lambda h d
+        float lh, lhe;
+        two_prod(lam, h, lh, lhe);
+        two_prod(lh, d[j], p, pe);
+        two_sum(sh, -p, sh, e);
+        sl += e - pe - lhe * d[j];
+      }
     }
+    r[i] = sh + sl;
   }
-  bool rok;
-  const float r32 = d2f_approx(r, &rok);
-  float rr[6];
+  chol6_solve(A, inv, r);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) rr[k] = __shfl_sync(0xffffffffu, (rok || r == 0.0) ? r32 : 0.0f, k);
-  chol6_solve(L, inv, rr, cor);
-  // refined step in FP64 (lanes 0-5) and its squared norms (lane 0: rho, lane 1: phi)
-  double dk = 0.0;
-  if (lane < 6) {
-    float a = d32[0], b = cor[0];
-#pragma unroll
-    for (int k = 1; k < 6; ++k) {
-      a = lane == k ? d32[k] : a;
-      b = lane == k ? cor[k] : b;
-    }
-    dk = f2d_exact(a) + f2d_exact(b);
-  }
-  const double e0 = shfl_d(dk, (lane & 1) * 3), e1 = shfl_d(dk, (lane & 1) * 3 + 1), e2 = shfl_d(dk, (lane & 1) * 3 + 2);
-  const double sq = fma(e0, e0, fma(e1, e1, e2 * e2));  // lane parity selects rho or phi
-  const double nr2 = shfl_d(sq, 0), th2 = shfl_d(sq, 1);
-  const double inf = __longlong_as_double(0x7FF0000000000000ll);
-  if (!ok || !nonneg_less(nr2, inf) || !nonneg_less(th2, inf) ||
-      (nonneg_less(nr2, c.eps_t2) && nonneg_less(th2, c.eps_r2))) {
+  for (int q = 0; q < 6; ++q) d[q] += r[q];  // the refined step
+  const float nr2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+  const float p0 = d[3], p1 = d[4], p2 = d[5];
+  const float t2 = fmaf(p0, p0, fmaf(p1, p1, p2 * p2));
+  if (!ok || !(nr2 < 3.0e38f) || !(t2 < 3.0e38f) || (nr2 < c.eps_t2f && t2 < c.eps_r2f)) {
     if (lane == 0) {
       S.info.converged[level] = 1;
       S.done = 1;
@@ -375,13 +357,7 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
     __syncwarp();
     return;
   }
-  // exponential map minus identity in FP32 (every lane): Er = A K + B K^2,
-  // et = rho + B K rho + C K^2 rho, with K v = phi x v
-  float dl[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) dl[k] = d32[k] + cor[k];
-  const float p0 = dl[3], p1 = dl[4], p2 = dl[5];
-  const float t2 = fmaf(p0, p0, fmaf(p1, p1, p2 * p2));
+  // exponential map minus identity: A, B, C of theta^2
   float cA, cB, cC;
   if (t2 < 0.01f) {  // Taylor series in theta^2, enough terms for FP32 below theta = 0.1
     cA = fmaf(t2, fmaf(t2, fmaf(t2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
@@ -395,33 +371,37 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
     cB = (1.0f - cs) / t2;
     cC = (th - sn) / (t2 * th);
   }
-  const float K[9] = {0.0f, -p2, p1, p2, 0.0f, -p0, -p1, p0, 0.0f};
-  float Er[9];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const float k2 = (i == j ? -t2 : 0.0f) + dl[3 + i] * dl[3 + j];  // K^2 = phi phi^T - theta^2 I
-      Er[i * 3 + j] = fmaf(cA, K[i * 3 + j], cB * k2);
-    }
-  const float kr0 = p1 * dl[2] - p2 * dl[1], kr1 = p2 * dl[0] - p0 * dl[2], kr2 = p0 * dl[1] - p1 * dl[0];
-  const float kk0 = p1 * kr2 - p2 * kr1, kk1 = p2 * kr0 - p0 * kr2, kk2 = p0 * kr1 - p1 * kr0;
-  const float et[3] = {fmaf(cC, kk0, fmaf(cB, kr0, dl[0])), fmaf(cC, kk1, fmaf(cB, kr1, dl[1])),
-                       fmaf(cC, kk2, fmaf(cB, kr2, dl[2]))};
-  // Tc = T + [Er | et] T in FP64 (lanes 0-11: rows 0-2, columns 0-3)
+  // increment (exp(d) - I) T in FP32 from the float pose, added to the pose
+  // carried as float pairs (lanes 0-11: rows 0-2, columns 0-3).  Row i of
+  // exp(d) - I: Er = A K + B K^2 with K v = phi x v and K^2 = phi phi^T -
+  // theta^2 I; et = rho + B K rho + C K^2 rho.
   if (lane < 12) {
     const int i = lane >> 2, j = lane & 3;
-    double v = S.T[i * 4 + j];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {  // row i of Er selected without indexing registers at run time
-      const float e = i == 0 ? Er[k] : (i == 1 ? Er[3 + k] : Er[6 + k]);
-      v = fma(f2d_exact(e), S.T[k * 4 + j], v);
+    const float pi = i == 0 ? p0 : (i == 1 ? p1 : p2);
+    // row i of K: (K_i0, K_i1, K_i2)
+    const float k0 = i == 0 ? 0.0f : (i == 1 ? p2 : -p1);
+    const float k1 = i == 0 ? -p2 : (i == 1 ? 0.0f : p0);
+    const float k2 = i == 0 ? p1 : (i == 1 ? -p0 : 0.0f);
+    const float e0 = fmaf(cA, k0, cB * fmaf(pi, p0, i == 0 ? -t2 : 0.0f));
+    const float e1 = fmaf(cA, k1, cB * fmaf(pi, p1, i == 1 ? -t2 : 0.0f));
+    const float e2 = fmaf(cA, k2, cB * fmaf(pi, p2, i == 2 ? -t2 : 0.0f));
+    const float c0 = S.Rf[j < 3 ? j : 9], c1 = S.Rf[j < 3 ? 3 + j : 10], c2 = S.Rf[j < 3 ? 6 + j : 11];
+    float inc = fmaf(e0, c0, fmaf(e1, c1, e2 * c2));
+    if (j == 3) {  // + (rho + B K rho + C K^2 rho)_i
+      const float kr = fmaf(k0, d[0], fmaf(k1, d[1], k2 * d[2]));  // (K rho)_i
+      const float kr0 = p1 * d[2] - p2 * d[1], kr1 = p2 * d[0] - p0 * d[2], kr2 = p0 * d[1] - p1 * d[0];
+      const float kk = fmaf(k0, kr0, fmaf(k1, kr1, k2 * kr2));  // (K K rho)_i
+      const float rho_i = i == 0 ? d[0] : (i == 1 ? d[1] : d[2]);
+      inc += fmaf(cC, kk, fmaf(cB, kr, rho_i));
     }
-    if (j == 3) v += f2d_exact(i == 0 ? et[0] : (i == 1 ? et[1] : et[2]));
-    S.Tc[lane] = v;
-    S.Rcf[j < 3 ? i * 3 + j : 9 + i] = (float)v;
+    const int fi = j < 3 ? i * 3 + j : 9 + i;
+    float hi, lo;
+    two_sum(S.Rf[fi], inc, hi, lo);
+    lo += S.Rlf[fi];
+    const float h2 = hi + lo;  // renormalised: h2 is the nearest float of the pair's sum
+    S.Rcf[fi] = h2;
+    S.Rclf[fi] = lo - (h2 - hi);
   }
-  if (lane >= 12 && lane < 16) S.Tc[lane] = lane == 15 ? 1.0 : 0.0;
   __syncwarp();
 }
 
@@ -446,26 +426,29 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const DevFrame& f = d.f;
   const DevParams& p = d.p;
-  if (threadIdx.x < 16) {
-    S.T[threadIdx.x] = d.T_init[threadIdx.x];
-    S.Tc[threadIdx.x] = d.T_init[threadIdx.x];
-  }
+
   if (threadIdx.x == 0) {
     S.done = 0;
-    S.E = 0.0;
+    S.Ef = 0.0f;
     S.N = 0;
-    S.fin_E = 0.0;
+    S.fin_E = 0.0f;
     S.fin_N = 0;
-    S.lambda = 0.0;
+    S.lam_k = 0;
+    S.moved = 0;
     rf_track_info z = {};
     S.info = z;
   }
   __syncthreads();
-  if (threadIdx.x < 12) {
+  if (threadIdx.x < 12) {  // the initial pose as float pairs (FP64 once per registration)
     const int i = threadIdx.x < 9 ? threadIdx.x / 3 : threadIdx.x - 9;
     const int j = threadIdx.x < 9 ? threadIdx.x % 3 : 3;
-    S.Rf[threadIdx.x] = (float)S.T[i * 4 + j];
-    S.Rcf[threadIdx.x] = S.Rf[threadIdx.x];
+    const double t = d.T_init[i * 4 + j];
+    S.T0[threadIdx.x] = t;
+    const float hi = (float)t;
+    S.Rf[threadIdx.x] = hi;
+    S.Rlf[threadIdx.x] = (float)(t - (double)hi);
+    S.Rcf[threadIdx.x] = hi;
+    S.Rclf[threadIdx.x] = S.Rlf[threadIdx.x];
   }
   __syncthreads();
   int eval = 0;
@@ -622,10 +605,16 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
     }
   }
   if (lb == 0) {
-    if (threadIdx.x < 16) d.T_out[threadIdx.x] = S.T[threadIdx.x];
+    if (threadIdx.x < 16) {  // the pose in FP64: hi + lo of each entry, the last row 0 0 0 1
+      const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
+      const int fi = j < 3 ? i * 3 + j : 9 + i;
+      d.T_out[threadIdx.x] = i == 3   ? (j == 3 ? 1.0 : 0.0)
+                             : S.moved ? (double)S.Rf[fi] + (double)S.Rlf[fi]
+                                       : S.T0[fi];
+    }
     if (threadIdx.x == 0 && d.info) {
       rf_track_info out = S.info;
-      out.final_cost = S.fin_N > 0 ? S.fin_E / (double)S.fin_N : 0.0;
+      out.final_cost = S.fin_N > 0 ? (double)S.fin_E / (double)S.fin_N : 0.0;
       out.final_valid = S.fin_N;
       *d.info = out;
     }
@@ -682,8 +671,10 @@ RegDesc make_reg_desc(rf_volume* vol, const DevFrame& f, const double* T_init, c
   d.c.lambda0 = vol->p.lm_lambda0;
   d.c.eps_t = vol->p.lm_eps_trans;
   d.c.eps_r = vol->p.lm_eps_rot;
-  d.c.eps_t2 = vol->p.lm_eps_trans * vol->p.lm_eps_trans;
-  d.c.eps_r2 = vol->p.lm_eps_rot * vol->p.lm_eps_rot;
+  d.c.eps_t2f = (float)(vol->p.lm_eps_trans * vol->p.lm_eps_trans);
+  d.c.eps_r2f = (float)(vol->p.lm_eps_rot * vol->p.lm_eps_rot);
+  for (int k = -kLambdaPow; k <= kLambdaPow; ++k)
+    d.c.lambda_pow[k + kLambdaPow] = (float)(vol->p.lm_lambda0 * std::pow(10.0, (double)k));
   d.c.min_valid = vol->p.lm_min_valid;
   for (int l = 0; l < 3; ++l) {
     d.c.iters[l] = vol->p.lm_iters[l];

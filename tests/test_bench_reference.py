@@ -1,5 +1,5 @@
 """The benchmark's reference arm on the CPU: `bench.py --impl reference`
-times the FP64 oracle on a bounded window of each frame and prints one JSON
+times the FP64 oracle on whole 640x480 frames, one per step, and prints one JSON
 line with the contract's keys (no GPU involved)."""
 import json
 import os

@@ -422,11 +422,14 @@ def test_invalid_arguments(R):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("batch_group", [0, 2])
-def test_batch_is_bit_identical_to_single_streams(R, batch_group):
+def test_batch_is_bit_identical_to_single_streams(R, O, batch_group):
     """Three streams of different resolution, intrinsics and voxel size: the
     batched path gives exactly the poses, masks and volumes of the streams
     processed alone (partial sums over fixed pixel chunks), whether their
-    registrations share one launch or run in groups of two."""
+    registrations share one launch or run in groups of two; and (one launch)
+    every frame of every stream matches the oracle run in lockstep: poses
+    within 1e-4 m / 1e-4 rad, masks to 1e-3 of the pixels, final volumes with
+    exact blocks, weights and colours and the SDF within 1e-4 tau."""
     from synth.scenes import CAM_QVGA
     specs = [("tiny", 0, None, 0.02), ("dynamic", 1, CAM_QVGA, 0.03), ("static", 2, None, 0.01)]
     seqs = [make_sequence(c, sd, n_frames=4, camera=cam) for c, sd, cam, _ in specs]
@@ -471,6 +474,25 @@ def test_batch_is_bit_identical_to_single_streams(R, batch_group):
     for sa, sb in zip(outs["single"][2], outs["batch"][2]):
         for key in ("coords", "F", "W", "rgb", "wc"):
             np.testing.assert_array_equal(sa[key], sb[key])
+    if batch_group == 0:
+        poses, masks, snaps = outs["batch"]
+        for k, (s, (_, _, _, vx)) in enumerate(zip(seqs, specs)):
+            check_against_oracle(O, s, [poses[i][k] for i in range(4)], [masks[i][k] for i in range(4)],
+                                 snaps[k], vx)
+
+
+def check_against_oracle(O, seq, poses, masks, snap, voxel, fp16=False):
+    """The frames of one stream as served (poses, masks, final volume) against
+    the oracle in lockstep (tests/_oracle_lockstep.py; poses gated after the
+    oracle's convergence, check_rows)."""
+    from ._oracle_lockstep import assert_volume_matches, check_rows, replay
+    n = len(poses)
+    frames = [seq.frame(i)[:2] for i in range(n)]
+    T_in = [seq.frame(0)[2]] + [poses[i - 1] for i in range(1, n)]
+    orc, rows = replay(O, frames, seq.camera, T_in, poses, [None] + list(masks[1:]), voxel, TAU, fp16)
+    check_rows(rows, POSE_TOL)
+    f_tol = (2.0 ** -11 + 1e-5) * TAU if fp16 else 1e-4 * TAU
+    return rows, assert_volume_matches(snap, orc.export(), TAU, f_tol)
 
 
 @pytest.mark.gpu

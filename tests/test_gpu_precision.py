@@ -35,6 +35,7 @@ pytestmark = pytest.mark.gpu
 
 TAU = P.TAU
 HALF_UNIT = 2.0 ** -12
+R_FP32, R_FP16 = 0, 1  # rf_params.storage (RF_STORAGE_FP32, RF_STORAGE_FP16)
 
 
 @pytest.fixture(scope="module")
@@ -170,13 +171,15 @@ def test_fp16_tracking_vs_oracle(R, O):
     print(f"FP16 storage: pose vs oracle {worst[0]:.2e} m, {worst[1]:.2e} rad")
 
 
-def _batch_vs_single(R, specs, n_frames, n_buckets, max_blocks):
-    """Each stream's poses, masks and final volume from one FP16 batch, and
-    from rf_process_frame on the stream alone, must be identical."""
+def _batch_vs_single(R, specs, n_frames, n_buckets, max_blocks, O=None, storage=R_FP16):
+    """Each stream's poses, masks and final volume from one batch, and from
+    rf_process_frame on the stream alone, must be identical; with O, every
+    stream's frames must also match the oracle run in lockstep."""
     seqs = [make_sequence(c, sd, n_frames=n_frames, camera=cam) for c, sd, cam, _ in specs]
     outs = {}
     for mode in ("single", "batch"):
-        vols = [fp16_volume(R, s.camera, vx, n_buckets=n_buckets, max_blocks=max_blocks)
+        vols = [(fp16_volume if storage == R_FP16 else P.gpu_volume)(R, s.camera, vx, n_buckets=n_buckets,
+                                                                      max_blocks=max_blocks)
                 for s, (_, _, _, vx) in zip(seqs, specs)]
         batch = R.Batch(vols) if mode == "batch" else None
         T = [None] * len(seqs)
@@ -211,6 +214,16 @@ def _batch_vs_single(R, specs, n_frames, n_buckets, max_blocks):
     for sa, sb in zip(outs["single"][2], outs["batch"][2]):
         for key in ("coords", "F", "W", "rgb", "wc"):
             np.testing.assert_array_equal(sa[key], sb[key])
+    if O is not None:
+        poses, masks, snaps = outs["batch"]
+        for k, (s, (_, _, _, vx)) in enumerate(zip(seqs, specs)):
+            rows, ferr = P.check_against_oracle(O, s, [poses[i][k] for i in range(n_frames)],
+                                                [masks[i][k] for i in range(n_frames)], snaps[k], vx,
+                                                fp16=storage == R_FP16)
+            print(f"stream {k} ({s.camera.width}x{s.camera.height}): worst pose vs oracle "
+                  f"{max(r.dt for r in rows):.2e} m {max(r.dr for r in rows):.2e} rad, mask mismatch "
+                  f"{max(r.mask for r in rows):.2e}, SDF {ferr:.2e} m, converged "
+                  f"{sum(r.converged for r in rows[1:])} of {len(rows) - 1}")
     return outs
 
 
@@ -218,12 +231,17 @@ def test_fp16_batch_is_bit_identical_to_single_streams(R):
     _batch_vs_single(R, [("tiny", 0, None, 0.02), ("dynamic", 1, CAM_QVGA, 0.03)], 4, 1 << 16, 100000)
 
 
-def test_fp16_batch_full_size_serving_resolutions(R):
-    """The serving workload's three resolutions in one FP16 batch at full
-    size: 1280x720 at 2 cm, 640x480 with movers at 1 cm, 320x240 with movers
-    at 3 cm; three frames each, identical to each stream alone."""
+@pytest.mark.parametrize("storage", ["fp16", "fp32"])
+def test_batch_full_size_serving_resolutions(R, O, storage):
+    """The serving workload's three resolutions in one batch at full size:
+    1280x720 at 2 cm, 640x480 with movers at 1 cm, 320x240 with movers at
+    3 cm; three frames each, identical to each stream alone, and every frame
+    of every stream against the oracle in lockstep (poses within 1e-4, masks
+    to 1e-3, blocks, weights and colours exact, SDF within 1e-4 tau for FP32
+    and one FP16 step of F / tau for FP16)."""
     outs = _batch_vs_single(R, [("precision", 0, CAM_HD, 0.02), ("dynamic", 1, CAM_VGA, 0.01),
-                                ("dynamic", 2, CAM_QVGA, 0.03)], 3, 1 << 18, 200000)
+                                ("dynamic", 2, CAM_QVGA, 0.03)], 3, 1 << 18, 200000, O=O,
+                            storage=R_FP16 if storage == "fp16" else R_FP32)
     assert all(len(s["coords"]) > 100 for s in outs["batch"][2])  # ~770, ~7900, ~270 blocks
 
 
