@@ -340,11 +340,21 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
 
 // Lighter grid barrier for kernels that synchronise many times: one counter
 // that only grows (zeroed before the launch); the k-th barrier waits until it
-// reaches k * nblocks.  Arrival is a fence plus one atomic add, waiting is an
-// acquire load.  Bounded like grid_barrier.
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+// reaches k * nblocks.  Arrival is one release reduction, waiting a poll with
+// relaxed loads.  Bounded like grid_barrier.
+//
+// Why relaxed polling: on this GPU an acquire at GPU scope also invalidates
+// the SM's L1, which holds the model the registration's samples gather; with
+// one barrier per cost evaluation every evaluation would start with a cold L1
+// (measured: the first sample's lookup took 2-5k cycles).  Nothing read after
+// the barrier needs L1 invalidated: the data other CTAs wrote before arriving
+// (the partial sums) is read with L2-only loads (ld.global.cg) after the poll
+// has observed the count, and the writers' release reduction made those
+// writes visible at L2 before the count; the model is not written while the
+// registration runs.
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
   unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -362,7 +372,7 @@ __device__ __forceinline__ bool grid_sync_counter(unsigned* count, unsigned targ
     red_release_gpu_add(count, 1u);
     int ok = 1;
     long long spins = 0;
-    while (ld_acquire_gpu(count) < target) {
+    while (ld_relaxed_gpu(count) < target) {
       if (++spins > spin_limit) {
         ok = 0;
         atomicOr(status, ST_BARRIER);
