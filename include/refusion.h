@@ -25,7 +25,7 @@
  *    except rf_volume_export/import staging on the host.
  *  - Errors: each call returns an rf_status.  Argument errors are detected on
  *    the host before anything is enqueued.  Errors found by kernels (hash or
- *    pool full, candidate overflow, flood fill not converged, barrier timeout)
+ *    pool full, candidate overflow, flood fill not converged, grid-wide wait timeout)
  *    are OR-ed into a per-volume device status word; rf_sync_status()
  *    synchronises the stream, returns the first such error and clears it.
  *    rf_last_error() gives a readable message for the last failing call.
@@ -50,7 +50,7 @@ typedef enum rf_status {
   RF_ERR_CUDA = 2,             /* a CUDA runtime call failed (message in rf_last_error) */
   RF_ERR_HASH_FULL = 3,        /* bounded hash probe found no free slot */
   RF_ERR_POOL_FULL = 4,        /* more blocks than max_blocks */
-  RF_ERR_NOT_CONVERGED = 5,    /* flood fill exceeded max_ff_sweeps, or a grid barrier timed out */
+  RF_ERR_NOT_CONVERGED = 5,    /* flood fill exceeded max_ff_sweeps, or a grid-wide wait timed out */
   RF_ERR_BUFFER_TOO_SMALL = 6, /* caller buffer smaller than the result */
   RF_ERR_OUT_OF_RANGE = 7,     /* block coordinate outside +-8191 blocks per axis */
   RF_ERR_CAPACITY = 8          /* frustum candidate list overflow (raise max_candidates) */
@@ -331,17 +331,28 @@ rf_status rf_get_launch_config(rf_volume* vol, rf_launch_config* out);
 rf_status rf_set_launch_config(rf_volume* vol, const rf_launch_config* cfg);
 
 /* Bounded waits (a property of the library; the paper has no counterpart).
- * Every grid-wide barrier of the cooperative kernels (registration, flood
- * fill) polls at most spin_limit times before it gives up: the kernel then
- * records RF_ERR_NOT_CONVERGED in the status word (rf_sync_status) and
+ * Every grid-wide wait of the cooperative kernels (the flood fill's grid
+ * barrier; the registration's wait for every CTA's partial sums of a cost
+ * evaluation) polls at most spin_limit times before it gives up: the kernel
+ * then records RF_ERR_NOT_CONVERGED in the status word (rf_sync_status) and
  * returns, and the volume stays usable.  spin_limit 0 restores the default,
  * 2^24 polls (about one second).  extra_arrivals is fault injection for
- * tests: with extra_arrivals > 0 each barrier waits for that many arrivals
- * beyond the CTAs launched, which never come, so every wait runs out and the
- * error path is exercised; use 0 otherwise.  Synchronises the device and
+ * tests: with extra_arrivals > 0 each wait expects that many arrivals beyond
+ * the CTAs launched, which never come, so every wait runs out and the error
+ * path is exercised; use 0 otherwise.  Synchronises the device and
  * drops the volume's captured graphs; batches keep the limits in force when
  * they first saw a frame shape. */
 rf_status rf_set_wait_limits(rf_volume* vol, int64_t spin_limit, int extra_arrivals);
+
+/* Registration tags (a property of the library; the paper has no
+ * counterpart).  Each cost evaluation of a registration publishes its partial
+ * sums tagged with a number from a per-volume sequence that only grows, and
+ * starts over at 0, with the partial-sum buffer cleared, before it would reach
+ * 2^31.  This call sets the sequence's next base (clearing the buffer, so no
+ * stale tag can match), which lets tests reach the restart without 2^31
+ * evaluations.  base must be at most 2^31 - 1 - (3 + the sum of lm_iters);
+ * synchronises the device. */
+rf_status rf_set_registration_tag_base(rf_volume* vol, uint32_t base);
 
 /* Enables (1) or disables (0) device timing of the whole-frame calls: CUDA
  * events recorded on the caller's stream (kept inside the captured graphs)

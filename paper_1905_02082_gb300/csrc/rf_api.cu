@@ -140,7 +140,9 @@ template <class Alloc>
 rf_status volume_buffers(rf_volume* vol, const rf_params* p, int64_t n_buckets, int64_t max_blocks, int max_width,
                          int max_height, Alloc&& A) {
   const size_t npix = (size_t)max_width * max_height;
-  const size_t max_chunks = (npix + 127) / 128;  // the smallest registration chunk
+  // partial-sum slots per component: the chunks of the smallest registration
+  // chunk (128 pixels)
+  const size_t max_slots = (npix + 127) / 128;
   const size_t ntiles = ((size_t)(max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
   const size_t nslots = (size_t)n_buckets * kSlots;
   rf_status s;
@@ -148,8 +150,8 @@ rf_status volume_buffers(rf_volume* vol, const rf_params* p, int64_t n_buckets, 
       (s = A(&vol->d_W, p->storage == RF_STORAGE_FP32 ? (size_t)max_blocks * kBV : 1, "weights")) ||
       (s = A(&vol->d_coords, (size_t)max_blocks, "coords")) ||
       (s = A(&vol->d_nbr, 2 * (size_t)max_blocks, "neighbour tables")) || (s = A(&vol->d_nblocks, 1, "pool")) ||
-      (s = A(&vol->d_status, 1, "status")) || (s = A(&vol->d_regbar, 2, "barrier")) ||
-      (s = A(&vol->d_partials, 2 * 29 * max_chunks + 2, "partials")) || (s = A(&vol->d_seeds, npix, "seeds")) ||
+      (s = A(&vol->d_status, 1, "status")) || (s = A(&vol->d_regtags, 3, "registration tags")) ||
+      (s = A(&vol->d_partials, 2 * 29 * max_slots, "partials")) || (s = A(&vol->d_seeds, npix, "seeds")) ||
       (s = A(&vol->d_md, npix, "mask work")) || (s = A(&vol->d_ff, (size_t)p->max_ff_sweeps + 2, "flood-fill words")) ||
       (s = A(&vol->d_integ, 1, "integ")) || (s = A(&vol->d_tilemax, ntiles, "tiles")) ||
       (s = A(&vol->d_dmask, npix, "masked depth")) ||
@@ -243,7 +245,7 @@ rf_status status_from_bits(rf_volume* vol, unsigned bits) {
   if (bits & ST_POOL_FULL) return set_error(vol, RF_ERR_POOL_FULL, "block pool full (max_blocks reached)");
   if (bits & ST_CAPACITY) return set_error(vol, RF_ERR_CAPACITY, "frustum candidate list overflow");
   if (bits & ST_OUT_OF_RANGE) return set_error(vol, RF_ERR_OUT_OF_RANGE, "block coordinate outside +-8191");
-  if (bits & ST_BARRIER) return set_error(vol, RF_ERR_NOT_CONVERGED, "grid barrier timed out");
+  if (bits & ST_BARRIER) return set_error(vol, RF_ERR_NOT_CONVERGED, "grid-wide wait timed out (flood-fill barrier or registration partial sums)");
   if (bits & ST_NOT_CONVERGED) return set_error(vol, RF_ERR_NOT_CONVERGED, "flood fill exceeded max_ff_sweeps");
   return set_error(vol, RF_ERR_CUDA, "unknown device status 0x%x", bits);
 }
@@ -513,6 +515,7 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     rf_volume* v = b->vols[i];
     flood[i] = make_flood_desc(v, f[i]);
     mdesc[i] = make_mask_desc(v, f[i], v->d_T + 16, v->d_mask);
+    mdesc[i].pxcache = nullptr;  // batches keep no pixel block cache
   }
   e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
   if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);
@@ -542,7 +545,6 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     for (int i = 0; i < n; ++i) max_npix = std::max(max_npix, f[i].H * f[i].W);
     const dim3 copy_grid((unsigned)std::min((max_npix * 3 / 16 + 255) / 256, 64), (unsigned)n);
     k_batch_stage<<<copy_grid, 256, 0, cs>>>(table);
-    for (int i = 0; i < n; ++i) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
     for (int gi = 0; gi < out->ngroups && !s; ++gi)
       s = launch_register_batch(b->vols[0], out->d_desc, maps + gi * map_len, maps + gi * map_len + out->total_ctas,
                                 out->total_ctas, cs);
@@ -554,7 +556,6 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
       s = launch_floodfill_batch(b->vols[0], out->d_flood, ff_maps + gi * ff_len,
                                  ff_maps + gi * ff_len + out->ff_ctas, out->ff_ctas, cs);
     if (!s) s = launch_mask_post_batch(b->vols[0], out->d_mask, n, max_npix, cs);
-    for (int i = 0; i < n; ++i) cudaMemsetAsync(b->vols[i]->d_regbar, 0, 2 * sizeof(unsigned), cs);
     for (int gi = 0; gi < out->ngroups && !s; ++gi)
       s = launch_register_batch(b->vols[0], out->d_desc + n, maps + gi * map_len,
                                 maps + gi * map_len + out->total_ctas, out->total_ctas, cs);
@@ -640,7 +641,7 @@ rf_status rf_destroy_volume(rf_volume* vol) {
   for (auto& e : vol->ev)
     if (e) cudaEventDestroy(e);
   void* dev[] = {vol->d_hash, vol->d_vox,  vol->d_W,       vol->d_coords, vol->d_nbr, vol->d_nblocks, vol->d_status,
-                 vol->d_regbar, vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
+                 vol->d_regtags, vol->d_partials, vol->d_seeds, vol->d_md,    vol->d_ff,      vol->d_integ,
                  vol->d_tilemax, vol->d_cand, vol->d_depth, vol->d_rgb,   vol->d_mask,    vol->d_T, vol->d_info,
                  vol->d_guard, vol->d_pxcache, vol->d_dmask};
   for (void* p : dev)
@@ -671,7 +672,7 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
     return s;
   }
   const size_t npix = (size_t)max_width * max_height;
-  vol->max_chunks = (int)((npix + 127) / 128);
+  vol->max_slots = (int)((npix + 127) / 128);
   vol->reg_grid = register_max_grid(vol->device);
   if (vol->reg_grid > vol->sm_count) vol->reg_grid = vol->sm_count;
   if (vol->reg_grid < 1) {
@@ -702,6 +703,11 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
   if (vol->ff_grid < 1) vol->ff_grid = 1;
   s = clear_model(vol, 0);
   if (!s) s = check_cuda(vol, cudaMemset(vol->d_status, 0, sizeof(unsigned)), "status reset");
+  // registration tags start at 0 (base, counts) with every partial-sum word's tag 0
+  if (!s) s = check_cuda(vol, cudaMemset(vol->d_regtags, 0, 3 * sizeof(unsigned)), "tag reset");
+  if (!s)
+    s = check_cuda(vol, cudaMemset(vol->d_partials, 0, (size_t)2 * 29 * vol->max_slots * sizeof(unsigned long long)),
+                   "partials reset");
   if (!s) s = check_cuda(vol, cudaDeviceSynchronize(), "create sync");
   if (s) {
     g_create_error = vol->last_error;
@@ -1020,6 +1026,21 @@ rf_status rf_set_wait_limits(rf_volume* vol, int64_t spin_limit, int extra_arriv
   vol->wait_spins = spin_limit == 0 ? kDefaultSpinLimit : (long long)spin_limit;
   vol->wait_extra = (unsigned)extra_arrivals;
   return RF_OK;
+}
+
+rf_status rf_set_registration_tag_base(rf_volume* vol, uint32_t base) {
+  if (!vol) return RF_ERR_INVALID_ARG;
+  const uint64_t span = 3 + (uint64_t)vol->p.lm_iters[0] + vol->p.lm_iters[1] + vol->p.lm_iters[2];
+  if ((uint64_t)base + span >= (uint64_t)kTagLimit)
+    return set_error(vol, RF_ERR_INVALID_ARG, "tag base %u: must be below 2^31 - %llu", base,
+                     (unsigned long long)span);
+  rf_status s = check_cuda(vol, cudaDeviceSynchronize(), "tag base sync");
+  if (!s)
+    s = check_cuda(vol, cudaMemset(vol->d_partials, 0, (size_t)2 * 29 * vol->max_slots * sizeof(unsigned long long)),
+                   "partials reset");
+  const unsigned words[3] = {base, 0u, 0u};
+  if (!s) s = check_cuda(vol, cudaMemcpy(vol->d_regtags, words, sizeof(words), cudaMemcpyHostToDevice), "tag base");
+  return s;
 }
 
 rf_status rf_volume_stats(rf_volume* vol, rf_stats* out) {

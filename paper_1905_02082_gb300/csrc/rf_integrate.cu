@@ -712,19 +712,22 @@ __global__ void __launch_bounds__(kIntegThreads, 8) k_integrate(DevVol v, DevFra
 // Neighbour tables of the blocks allocated since `lo`: each new block gets
 // the pools of its 7 positive neighbours, and each existing negative
 // neighbour gets the new block in the matching slot.  Runs after the
-// integration (the hash is complete and read-only here).
-__device__ __forceinline__ void fixup_block(const DevVol& v, int b) {
+// integration (the hash is complete and read-only here).  One thread per
+// table entry (15 per new block: its own slot 0, 7 forward lookups, 7
+// reverse ones), so the hash probes of a block run side by side.  Two new
+// neighbours write each other's entries from both sides with the same value.
+constexpr int kFixupWork = 15;
+
+__device__ __forceinline__ void fixup_entry(const DevVol& v, int b, int k) {
   const int4 c = v.coords[b];
   if (c.w == 0) return;
   int* flat = reinterpret_cast<int*>(v.nbr);
-  int t[8];
-  t[0] = b;
-#pragma unroll
-  for (int o = 1; o < 8; ++o) t[o] = hash_find(v, c.x + (o & 1), c.y + ((o >> 1) & 1), c.z + ((o >> 2) & 1));
-  v.nbr[2 * (size_t)b] = make_int4(t[0], t[1], t[2], t[3]);
-  v.nbr[2 * (size_t)b + 1] = make_int4(t[4], t[5], t[6], t[7]);
-#pragma unroll
-  for (int o = 1; o < 8; ++o) {
+  if (k == 0) {
+    flat[8 * (size_t)b] = b;
+  } else if (k < 8) {
+    flat[8 * (size_t)b + k] = hash_find(v, c.x + (k & 1), c.y + ((k >> 1) & 1), c.z + ((k >> 2) & 1));
+  } else {
+    const int o = k - 7;
     const int n = hash_find(v, c.x - (o & 1), c.y - ((o >> 1) & 1), c.z - ((o >> 2) & 1));
     if (n >= 0) flat[8 * (size_t)n + o] = b;
   }
@@ -735,7 +738,9 @@ __global__ void __launch_bounds__(256) k_nbr_fixup(DevVol v, const int* __restri
   if (gated_off(gate, kModeFirst)) return;
   const int lo = lo_ptr ? *lo_ptr : lo_value;
   const int hi = min(*(volatile int*)v.n_blocks, v.max_blocks);
-  for (int b = lo + blockIdx.x * blockDim.x + threadIdx.x; b < hi; b += gridDim.x * blockDim.x) fixup_block(v, b);
+  const long long n = (long long)max(hi - lo, 0) * kFixupWork;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    fixup_entry(v, lo + (int)(i / kFixupWork), (int)(i % kFixupWork));
 }
 
 }  // namespace

@@ -30,7 +30,6 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr int kMaxProbe = 64;
 constexpr int kMaxCoord = 8191;  // |block coordinate| bound of the 14-bit key fields
 constexpr int kMaxPool = (1 << 22) - 2;
-constexpr int kPartialStride = 32;  // floats per CTA partial of the normal equations
 constexpr int kTile = 16;           // depth-max tiles used by the frustum cull
 
 // device status bits (OR-ed by kernels, read by rf_sync_status)
@@ -119,12 +118,18 @@ struct RegDesc {
   double* T_out;
   rf_track_info* info;
   LMConst c;
-  float* partials;
-  int max_chunks;
-  unsigned* bar;
+  // 2 x 29 x max_slots tagged partial sums (double-buffered by evaluation
+  // parity; component-major)
+  unsigned long long* partials;
+  int max_slots;
+  // tags[0]: the tag base of the next registration of this volume; tags[1]:
+  // CTAs that have left the current one; tags[2]: arrivals at the current
+  // one's evaluations (e * G after evaluation e).  The last CTA to leave
+  // clears both counts and advances the base past every tag it used.
+  unsigned* tags;
   unsigned* status;
-  long long spin_limit;  // bound of each grid-barrier wait (polls)
-  unsigned bar_extra;    // fault injection: arrivals each barrier waits for beyond the CTAs launched
+  long long spin_limit;  // bound of each wait (polls)
+  unsigned bar_extra;    // fault injection: arrivals each wait expects beyond the CTAs launched
   // per full-resolution pixel: the (block key << 22 | pool) its last sample
   // was found in, ~0 when none; a block's pool never changes until the
   // volume is reset or imported, which clear the cache.  nullptr: no cache
@@ -162,6 +167,7 @@ struct MaskDesc {
   unsigned* guard;
   uint8_t* md;
   uint8_t* mask_out;
+  const unsigned long long* pxcache;  // the volume's per-pixel block cache (read only)
 };
 
 __device__ __forceinline__ bool coord_ok(int bx, int by, int bz) {
@@ -206,13 +212,17 @@ __device__ __forceinline__ int hash_find(const DevVol& v, int bx, int by, int bz
 }
 
 
+// x < 2^23 as a float, exactly, without a conversion instruction: the float
+// with exponent 2^23 and mantissa x is 2^23 + x, and subtracting 2^23 is exact.
+__device__ __forceinline__ float u2f_exact(unsigned x) { return __uint_as_float(0x4B000000u | x) - 8388608.0f; }
+
 // 2126 R + 7152 G + 722 B as a float: the intensity of Sec. III-B times
 // 255e4 (exact integer arithmetic, one conversion).
 constexpr float kIntensityScale = 1.0f / 2550000.0f;
 __device__ __forceinline__ float rgb_intensity_raw(unsigned c) {
   // two 16x8-bit dot products: (2126, 7152) . (R, G) + (722, 0) . (B, byte 3)
   const unsigned s = __dp2a_hi(722u, c, __dp2a_lo(2126u | (7152u << 16), c, 0u));
-  return (float)s;
+  return u2f_exact(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,36 +267,75 @@ __device__ __forceinline__ double lerp_rn(double a, double b, double t) {
 // Fetches the 8 corner SDF values of the cell with lattice origin k; false if
 // any corner is missing or unobserved.  FP16 storage: the stored value F16 x
 // tau (one float multiply, exactly what rf_volume_export returns).
+// Pool of the block holding a lattice corner, from a block's neighbour table
+// (n0, n1: slots 0-7, slot dx + 2 dy + 4 dz): sx, sy, sz tell whether the
+// corner lies in the next block along x, y, z.  Selects only, so the table
+// stays in registers (an indexed array would go to local memory).
+__device__ __forceinline__ int nbr_pick(const int4& n0, const int4& n1, bool sx, bool sy, bool sz) {
+  const int a = sx ? n0.y : n0.x, b = sx ? n0.w : n0.z;
+  const int c = sx ? n1.y : n1.x, e = sx ? n1.w : n1.z;
+  const int lo = sy ? b : a, hi = sy ? e : c;
+  return sz ? hi : lo;
+}
+
+// The SDF values (metres) at the 8 corners n = dx + 2 dy + 4 dz of the
+// lattice cell whose corner 0 is voxel (lx, ly, lz) of block `pool`.  All
+// loads are issued before any value is tested, so their latencies overlap.
+// False if a corner's block is missing or a corner was never observed.
 template <int ST>
-__device__ __forceinline__ bool corners_of(const DevVol& v, const DevParams& p, int kx, int ky, int kz, float F[8]) {
-  const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
-  if (pool < 0) return false;
-  const int lx = kx & 7, ly = ky & 7, lz = kz & 7;
+__device__ __forceinline__ bool corners_at(const DevVol& v, const DevParams& p, int pool, int lx, int ly, int lz,
+                                           float F[8]) {
   auto value = [&](int pl, int i) -> float {
     if constexpr (ST == RF_STORAGE_FP32) return __uint_as_float(__ldg(&v.vox[(size_t)pl * kBV + i].x));
     else return trk_sdf(__ldg(trk_words(v, pl) + i), p.tau);
   };
   if (lx < 7 && ly < 7 && lz < 7) {  // all 8 corners in one block
     const int base = lx + 8 * ly + 64 * lz;
-    const int off[8] = {0, 1, 8, 9, 64, 65, 72, 73};
+#pragma unroll
+    for (int n = 0; n < 8; ++n) F[n] = value(pool, base + (n & 1) + 8 * ((n >> 1) & 1) + 64 * ((n >> 2) & 1));
+  } else {
+    const int4 n0 = __ldg(v.nbr + 2 * (size_t)pool), n1 = __ldg(v.nbr + 2 * (size_t)pool + 1);
+    const bool ex = lx == 7, ey = ly == 7, ez = lz == 7;
+    int pn[8];
+    bool present = true;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      F[n] = value(pool, base + off[n]);
-      if (F[n] != F[n]) return false;
+      pn[n] = nbr_pick(n0, n1, (n & 1) && ex, ((n >> 1) & 1) && ey, ((n >> 2) & 1) && ez);
+      present = present && pn[n] >= 0;
     }
-    return true;
-  }
-  const int4 n0 = __ldg(v.nbr + 2 * (size_t)pool), n1 = __ldg(v.nbr + 2 * (size_t)pool + 1);
-  const int nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+    if (!present) return false;
 #pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    const int ix = lx + (n & 1), iy = ly + ((n >> 1) & 1), iz = lz + ((n >> 2) & 1);
-    const int pn = nb[(ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3)];
-    if (pn < 0) return false;
-    F[n] = value(pn, (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
-    if (F[n] != F[n]) return false;
+    for (int n = 0; n < 8; ++n) {
+      const int ix = (lx + (n & 1)) & 7, iy = (ly + ((n >> 1) & 1)) & 7, iz = (lz + ((n >> 2) & 1)) & 7;
+      F[n] = value(pn[n], ix + 8 * iy + 64 * iz);
+    }
   }
-  return true;
+  bool observed = true;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) observed = observed && F[n] == F[n];
+  return observed;
+}
+
+template <int ST>
+__device__ __forceinline__ bool corners_of(const DevVol& v, const DevParams& p, int kx, int ky, int kz, float F[8]) {
+  const int pool = hash_find(v, kx >> 3, ky >> 3, kz >> 3);
+  if (pool < 0) return false;
+  return corners_at<ST>(v, p, pool, kx & 7, ky & 7, kz & 7, F);
+}
+
+// The same with a per-pixel cache of (block key << 22 | pool) entries: a
+// matching entry saves the hash probe (entries of other blocks are ignored).
+template <int ST>
+__device__ __forceinline__ bool corners_cached(const DevVol& v, const DevParams& p, int kx, int ky, int kz,
+                                               unsigned long long cached, float F[8]) {
+  const int bx = kx >> 3, by = ky >> 3, bz = kz >> 3;
+  int pool;
+  if (cached != kEmpty && coord_ok(bx, by, bz) && (cached >> 22) == pack_key(bx, by, bz))
+    pool = (int)(cached & 0x3FFFFFull);
+  else
+    pool = hash_find(v, bx, by, bz);
+  if (pool < 0) return false;
+  return corners_at<ST>(v, p, pool, kx & 7, ky & 7, kz & 7, F);
 }
 
 __device__ __forceinline__ bool pixel_valid(const DevParams& p, unsigned raw) {
@@ -338,53 +387,69 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
   return s_ok != 0;
 }
 
-// Lighter grid barrier for kernels that synchronise many times: one counter
-// that only grows (zeroed before the launch); the k-th barrier waits until it
-// reaches k * nblocks.  Arrival is one release reduction, waiting a poll with
-// relaxed loads.  Bounded like grid_barrier.
+// Registration exchange.  Every CTA of a registration writes its partial
+// sums of an evaluation as 64-bit words, the float in the low half and the
+// evaluation's tag in the high half, then counts itself in an arrival counter
+// with a relaxed reduction, and waits (one thread polling) until the count
+// shows every CTA.  No fence orders the partials before the count (a release
+// there cost a full L2 round trip per evaluation): the readers check each
+// word's tag instead and read again the rare word that has not arrived.  A
+// 64-bit access is single-copy atomic, so a word that shows the tag also
+// shows the partial written with it.
 //
-// Why relaxed polling: on this GPU an acquire at GPU scope also invalidates
-// the SM's L1, which holds the model the registration's samples gather; with
-// one barrier per cost evaluation every evaluation would start with a cold L1
-// (measured: the first sample's lookup took 2-5k cycles).  Nothing read after
-// the barrier needs L1 invalidated: the data other CTAs wrote before arriving
-// (the partial sums) is read with L2-only loads (ld.global.cg) after the poll
-// has observed the count, and the writers' release reduction made those
-// writes visible at L2 before the count; the model is not written while the
-// registration runs.
+// Accesses are relaxed at GPU scope (L1 bypassed).  On this GPU an acquire
+// at GPU scope also invalidates the SM's L1, which holds the model the
+// registration's samples gather; with one wait per cost evaluation every
+// evaluation would start with a cold L1 (measured: the first sample's lookup
+// took 2-5k cycles).  Nothing read after the wait needs it: the model is not
+// written while the registration runs.  (Letting every thread poll its
+// partials directly, without the count, was measured slower: tens of
+// thousands of polling threads congest the L2 slices the stragglers need.)
 __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-
-// Arrival: one release reduction by thread 0 after the CTA barrier (it
-// orders the CTA's earlier writes before the count, without a full fence).
-__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_relaxed_gpu_add(unsigned* p, unsigned v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync_counter(unsigned* count, unsigned target, unsigned* status,
-                                                  long long spin_limit) {
-  __shared__ int s_ok2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    red_release_gpu_add(count, 1u);
-    int ok = 1;
-    long long spins = 0;
-    while (ld_relaxed_gpu(count) < target) {
-      if (++spins > spin_limit) {
-        ok = 0;
-        atomicOr(status, ST_BARRIER);
-        break;
-      }
-      if (spins > 4096) __nanosleep(64);
-    }
-    s_ok2 = ok;
+// Polls *count until it reaches target, at most spin_limit times (after the
+// first 4,096 polls each followed by a 64 ns sleep); false when the wait ran
+// out.
+__device__ __forceinline__ bool await_count(const unsigned* count, unsigned target, long long spin_limit) {
+  long long spins = 0;
+  while (ld_relaxed_gpu(count) < target) {
+    if (++spins > spin_limit) return false;
+    if (spins > 4096) __nanosleep(64);
   }
-  __syncthreads();
-  return s_ok2 != 0;
+  return true;
 }
+
+// Waits until the tagged word *p (last read into v) carries tag `want`,
+// re-polling at most spin_limit times (the same schedule); false when the
+// wait ran out.
+__device__ __forceinline__ bool await_tag(const unsigned long long* p, unsigned long long& v, unsigned want,
+                                          long long spin_limit) {
+  long long spins = 0;
+  while ((unsigned)(v >> 32) != want) {
+    if (++spins > spin_limit) return false;
+    if (spins > 4096) __nanosleep(64);
+    v = ld_relaxed_gpu_u64(p);
+  }
+  return true;
+}
+
+// Tags stay below 2^31.
+constexpr unsigned kTagLimit = 0x80000000u;
 
 }  // namespace rf
 

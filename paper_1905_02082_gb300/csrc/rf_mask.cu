@@ -55,98 +55,139 @@ __device__ double residual_fp64(const DevVol& v, const DevFrame& f, const DevPar
   return __dmul_rn(V, V);
 }
 
-// Seeds of the 256 pixels of CTA `block` (blockDim.x = 256).
+// Seed decision of one valid pixel in FP32 with an error bound: 0 or 1, or
+// 2 when the lattice cell or the comparison lies within the bound (the pixel
+// is then decided in FP64).  Rf: the pose as floats (R row-major, then t).
+template <int ST>
+__device__ __forceinline__ int seed_fp32(const DevVol& v, const DevFrame& f, const DevParams& p, const float* Rf, int u,
+                                         int vv, unsigned raw, unsigned long long cached) {
+  const float t = p.gamma_tau2_f;
+  const float D = (float)raw * p.inv_depth_scale;
+  const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
+  float q[3], fr[3];
+  int k[3];
+  const float mag_in = (fabsf(x) + fabsf(y) + fabsf(D) + fabsf(Rf[9]) + fabsf(Rf[10]) + fabsf(Rf[11])) * p.inv_voxel;
+  float qmax = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float pi = Rf[i * 3] * x + Rf[i * 3 + 1] * y + Rf[i * 3 + 2] * D + Rf[9 + i];
+    q[i] = pi * p.inv_voxel;
+    qmax = fmaxf(qmax, fabsf(q[i]));
+  }
+  // bound on |q32 - q64| with an 8x margin (see the error budget in the design notes)
+  const float eps_q = (mag_in + qmax) * 3.814697265625e-06f;  // 2^-18
+  if (!(qmax < 8.0f * kMaxCoord - 2.0f)) return 2;
+  bool ambiguous = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float fl = floorf(q[i]);
+    k[i] = (int)fl;
+    fr[i] = q[i] - fl;
+    if (fr[i] < eps_q || fr[i] > 1.0f - eps_q) ambiguous = true;
+  }
+  if (ambiguous) return 2;
+  float F[8];
+  // an unambiguous cell with a missing corner is invalid in FP64 too: no seed
+  if (!corners_cached<ST>(v, p, k[0], k[1], k[2], cached, F)) return 0;
+  const float c00 = F[0] * (1.0f - fr[0]) + F[1] * fr[0], c10 = F[2] * (1.0f - fr[0]) + F[3] * fr[0];
+  const float c01 = F[4] * (1.0f - fr[0]) + F[5] * fr[0], c11 = F[6] * (1.0f - fr[0]) + F[7] * fr[0];
+  const float c0 = c00 * (1.0f - fr[1]) + c10 * fr[1], c1 = c01 * (1.0f - fr[1]) + c11 * fr[1];
+  const float V = fminf(fmaxf(c0 * (1.0f - fr[2]) + c1 * fr[2], -p.tau), p.tau);
+  float fmn = F[0], fmx = F[0], fab = fabsf(F[0]);
+#pragma unroll
+  for (int n = 1; n < 8; ++n) {
+    fmn = fminf(fmn, F[n]);
+    fmx = fmaxf(fmx, F[n]);
+    fab = fmaxf(fab, fabsf(F[n]));
+  }
+  // + the gap between the float and double truncation bounds (<= 2^-24 tau)
+  const float dV = 3.0f * (fmx - fmn) * eps_q + fab * 1.9073486328125e-06f + p.tau * 5.9604645e-08f;
+  const float r = V * V;
+  const float dr = 2.0f * fabsf(V) * dV + dV * dV + r * 2.384185791015625e-07f;  // 2^-22
+  if (fabsf(r - t) <= 2.0f * dr + t * 2.384185791015625e-07f) return 2;
+  return r > t ? 1 : 0;
+}
+
+// Seeds of the kSeedThreads * kSeedPx pixels of CTA `block` (blockDim.x =
+// kSeedThreads; pixel block * kSeedThreads * kSeedPx + j * kSeedThreads + tid
+// for j < kSeedPx).  Every thread first loads its pixels' depths and cache
+// entries, then decides them in FP32; the ambiguous ones are queued in shared
+// memory and decided in FP64 afterwards, side by side by consecutive threads:
+// on GB300 the FP64 pipe is narrow, and a warp that takes the FP64 branch for
+// one of its lanes costs as much as one that takes it for all 32.
+// pxcache: the registration's per-pixel block cache (nullptr: none), read
+// only, to skip hash probes.
+constexpr int kSeedThreads = 256;
+constexpr int kSeedPx = 4;
+
+__host__ __device__ constexpr int seed_blocks(int npix) {
+  return (npix + kSeedThreads * kSeedPx - 1) / (kSeedThreads * kSeedPx);
+}
+
 template <int ST>
 __device__ __forceinline__ void seeds_body(const DevVol& v, const DevFrame& f, const DevParams& p,
                                            const double* __restrict__ T, uint8_t* __restrict__ seeds,
-                                           unsigned* guard_count, int block) {
+                                           unsigned* guard_count, const unsigned long long* __restrict__ pxcache,
+                                           int block) {
   // pose and threshold converted once per CTA (conversions use the FP64 pipe)
   __shared__ float sR[12];
   __shared__ double s_t64;
+  __shared__ int s_queue[kSeedThreads * kSeedPx];
+  __shared__ int s_n;
   if (threadIdx.x < 12) {
     const int i = threadIdx.x < 9 ? threadIdx.x / 3 : threadIdx.x - 9;
     const int j = threadIdx.x < 9 ? threadIdx.x % 3 : 3;
     sR[threadIdx.x] = (float)T[i * 4 + j];
   }
   if (threadIdx.x == 12) s_t64 = __dmul_rn(__dmul_rn(p.gamma_d, p.tau_d), p.tau_d);
+  if (threadIdx.x == 13) s_n = 0;
   __syncthreads();
-  const int idx = block * blockDim.x + threadIdx.x;
-  if (idx >= f.H * f.W) return;
-  const int u = idx % f.W, vv = idx / f.W;
-  const unsigned raw = __ldg(f.depth + idx);
-  uint8_t seed = 0;
-  if (pixel_valid(p, raw)) {
-    const double t64 = s_t64;
-    const float t = p.gamma_tau2_f;
-    const float* Rf = sR;
-    const float D = (float)raw * p.inv_depth_scale;
-    const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
-    float q[3], fr[3];
-    int k[3];
-    bool ambiguous = false;
-    const float mag_in = (fabsf(x) + fabsf(y) + fabsf(D) + fabsf(Rf[9]) + fabsf(Rf[10]) + fabsf(Rf[11])) * p.inv_voxel;
-    float qmax = 0.0f;
+  const int npix = f.H * f.W;
+  const int first = block * kSeedThreads * kSeedPx + (int)threadIdx.x;
+  unsigned raw[kSeedPx];
+  unsigned long long cached[kSeedPx];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float pi = Rf[i * 3] * x + Rf[i * 3 + 1] * y + Rf[i * 3 + 2] * D + Rf[9 + i];
-      q[i] = pi * p.inv_voxel;
-      qmax = fmaxf(qmax, fabsf(q[i]));
-    }
-    // bound on |q32 - q64| with an 8x margin (see the error budget in the design notes)
-    const float eps_q = (mag_in + qmax) * 3.814697265625e-06f;  // 2^-18
-    if (!(qmax < 8.0f * kMaxCoord - 2.0f)) ambiguous = true;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float fl = floorf(q[i]);
-      k[i] = (int)fl;
-      fr[i] = q[i] - fl;
-      if (fr[i] < eps_q || fr[i] > 1.0f - eps_q) ambiguous = true;
-    }
-    if (!ambiguous) {
-      float F[8];
-      if (corners_of<ST>(v, p, k[0], k[1], k[2], F)) {
-        const float c00 = F[0] * (1.0f - fr[0]) + F[1] * fr[0], c10 = F[2] * (1.0f - fr[0]) + F[3] * fr[0];
-        const float c01 = F[4] * (1.0f - fr[0]) + F[5] * fr[0], c11 = F[6] * (1.0f - fr[0]) + F[7] * fr[0];
-        const float c0 = c00 * (1.0f - fr[1]) + c10 * fr[1], c1 = c01 * (1.0f - fr[1]) + c11 * fr[1];
-        const float V = fminf(fmaxf(c0 * (1.0f - fr[2]) + c1 * fr[2], -p.tau), p.tau);
-        float fmn = F[0], fmx = F[0], fab = fabsf(F[0]);
-#pragma unroll
-        for (int n = 1; n < 8; ++n) {
-          fmn = fminf(fmn, F[n]);
-          fmx = fmaxf(fmx, F[n]);
-          fab = fmaxf(fab, fabsf(F[n]));
-        }
-        // + the gap between the float and double truncation bounds (<= 2^-24 tau)
-        const float dV = 3.0f * (fmx - fmn) * eps_q + fab * 1.9073486328125e-06f + p.tau * 5.9604645e-08f;
-        const float r = V * V;
-        const float dr = 2.0f * fabsf(V) * dV + dV * dV + r * 2.384185791015625e-07f;  // 2^-22
-        if (fabsf(r - t) <= 2.0f * dr + t * 2.384185791015625e-07f) ambiguous = true;
-        else seed = r > t ? 1 : 0;
-      }
-      // an unambiguous cell with a missing corner is invalid in FP64 too: no seed
-    }
-    if (ambiguous) {
-      const double r64 = residual_fp64<ST>(v, f, p, T, u, vv, raw);
-      seed = (r64 >= 0.0 && r64 > t64) ? 1 : 0;
-      if (guard_count) atomicAdd(guard_count, 1u);
-    }
+  for (int j = 0; j < kSeedPx; ++j) {
+    const int idx = first + j * kSeedThreads;
+    raw[j] = idx < npix ? __ldg(f.depth + idx) : 0u;
+    cached[j] = idx < npix && pxcache ? __ldg(pxcache + idx) : kEmpty;
   }
-  seeds[idx] = seed;
+#pragma unroll 1
+  for (int j = 0; j < kSeedPx; ++j) {
+    const int idx = first + j * kSeedThreads;
+    if (idx >= npix) break;
+    const unsigned rj = j == 0 ? raw[0] : (j == 1 ? raw[1] : (j == 2 ? raw[2] : raw[3]));
+    const unsigned long long cj = j == 0 ? cached[0] : (j == 1 ? cached[1] : (j == 2 ? cached[2] : cached[3]));
+    int seed = 0;
+    if (pixel_valid(p, rj)) seed = seed_fp32<ST>(v, f, p, sR, idx % f.W, idx / f.W, rj, cj);
+    if (seed == 2) s_queue[atomicAdd(&s_n, 1)] = idx;
+    else seeds[idx] = (uint8_t)seed;
+  }
+  __syncthreads();
+  const int n = s_n;
+  for (int i = threadIdx.x; i < n; i += kSeedThreads) {
+    const int idx = s_queue[i];
+    const double r64 = residual_fp64<ST>(v, f, p, T, idx % f.W, idx / f.W, __ldg(f.depth + idx));
+    seeds[idx] = (r64 >= 0.0 && r64 > s_t64) ? 1 : 0;
+  }
+  if (threadIdx.x == 0 && n > 0 && guard_count) atomicAdd(guard_count, (unsigned)n);
 }
 
 template <int ST>
-__global__ void __launch_bounds__(256) k_seeds(DevVol v, DevFrame f, DevParams p, const double* __restrict__ T,
-                                               uint8_t* __restrict__ seeds, unsigned* guard_count) {
+__global__ void __launch_bounds__(kSeedThreads) k_seeds(DevVol v, DevFrame f, DevParams p,
+                                                        const double* __restrict__ T, uint8_t* __restrict__ seeds,
+                                                        unsigned* guard_count,
+                                                        const unsigned long long* __restrict__ pxcache) {
   if (gated_off(f.gate, kModeTrack)) return;
-  seeds_body<ST>(v, f, p, T, seeds, guard_count, blockIdx.x);
+  seeds_body<ST>(v, f, p, T, seeds, guard_count, pxcache, blockIdx.x);
 }
 
 // grid (x, n streams): the seeds of every tracked stream of a batch.
 template <int ST>
-__global__ void __launch_bounds__(256) k_seeds_batch(const MaskDesc* __restrict__ descs) {
+__global__ void __launch_bounds__(kSeedThreads) k_seeds_batch(const MaskDesc* __restrict__ descs) {
   const MaskDesc& d = descs[blockIdx.y];
-  if (gated_off(d.f.gate, kModeTrack) || (int)(blockIdx.x * blockDim.x) >= d.f.H * d.f.W) return;
-  seeds_body<ST>(d.v, d.f, d.p, d.T, d.seeds, d.guard, blockIdx.x);
+  if (gated_off(d.f.gate, kModeTrack) || (int)blockIdx.x >= seed_blocks(d.f.H * d.f.W)) return;
+  seeds_body<ST>(d.v, d.f, d.p, d.T, d.seeds, d.guard, d.pxcache, blockIdx.x);
 }
 
 __device__ __forceinline__ void erode_px(const uint8_t* __restrict__ in, int H, int W, uint8_t* __restrict__ mr,
@@ -297,9 +338,11 @@ rf_status launch_mask_pre(rf_volume* vol, const DevFrame& f, const double* T, cu
   rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_guard, 0, sizeof(unsigned), st), "guard reset");
   if (s != RF_OK) return s;
   if (vol->p.storage == RF_STORAGE_FP16)
-    k_seeds<RF_STORAGE_FP16><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds, vol->d_guard);
+    k_seeds<RF_STORAGE_FP16><<<seed_blocks(n), kSeedThreads, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds,
+                                                                       vol->d_guard, vol->d_pxcache);
   else
-    k_seeds<RF_STORAGE_FP32><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds, vol->d_guard);
+    k_seeds<RF_STORAGE_FP32><<<seed_blocks(n), kSeedThreads, 0, st>>>(vol->dv, f, vol->dp, T, vol->d_seeds,
+                                                                       vol->d_guard, vol->d_pxcache);
   k_erode<<<blocks, 256, 0, st>>>(vol->d_seeds, f.H, f.W, vol->d_md, f.gate);
   s = check_cuda(vol, cudaMemsetAsync(vol->d_ff, 0, sizeof(unsigned) * (2 + vol->p.max_ff_sweeps), st),
                  "flood-fill reset");
@@ -336,15 +379,17 @@ MaskDesc make_mask_desc(rf_volume* vol, const DevFrame& f, const double* T, uint
   d.guard = vol->d_guard;
   d.md = vol->d_md;
   d.mask_out = mask_out;
+  d.pxcache = vol->d_pxcache;
   return d;
 }
 
 rf_status launch_mask_pre_batch(rf_volume* vol, const MaskDesc* descs, int n, int max_npix, cudaStream_t st) {
   const dim3 grid((unsigned)((max_npix + 255) / 256), (unsigned)n);
+  const dim3 sgrid((unsigned)seed_blocks(max_npix), (unsigned)n);
   if (vol->p.storage == RF_STORAGE_FP16)
-    k_seeds_batch<RF_STORAGE_FP16><<<grid, 256, 0, st>>>(descs);
+    k_seeds_batch<RF_STORAGE_FP16><<<sgrid, kSeedThreads, 0, st>>>(descs);
   else
-    k_seeds_batch<RF_STORAGE_FP32><<<grid, 256, 0, st>>>(descs);
+    k_seeds_batch<RF_STORAGE_FP32><<<sgrid, kSeedThreads, 0, st>>>(descs);
   k_erode_batch<<<grid, 256, 0, st>>>(descs);
   return check_cuda(vol, cudaGetLastError(), "batched mask launch");
 }
@@ -475,9 +520,11 @@ extern "C" rf_status rf_compute_mask_noalloc(rf_volume* vol, const rf_frame* fra
   // the array keeps the previous call's contents: zero the words that count
   if ((s = check_cuda(vol, cudaMemsetAsync(ff, 0, sizeof(unsigned) * kNoAllocWords, st), "scratch clear"))) return s;
   if (vol->p.storage == RF_STORAGE_FP16)
-    k_seeds<RF_STORAGE_FP16><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard);
+    k_seeds<RF_STORAGE_FP16><<<seed_blocks(n), kSeedThreads, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard,
+                                                                       vol->d_pxcache);
   else
-    k_seeds<RF_STORAGE_FP32><<<blocks, 256, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard);
+    k_seeds<RF_STORAGE_FP32><<<seed_blocks(n), kSeedThreads, 0, st>>>(vol->dv, f, vol->dp, T_dev, seeds, guard,
+                                                                       vol->d_pxcache);
   k_erode<<<blocks, 256, 0, st>>>(seeds, f.H, f.W, md, nullptr);
   const int ntiles = ((f.W + kFFW - 1) / kFFW) * ((f.H + kFFH - 1) / kFFH);
   cudaLaunchConfig_t cfg = {};

@@ -11,17 +11,18 @@
 //      J = dV/dp [I | -[p]x] (left perturbation);
 //   2. a warp-shuffle + shared-memory reduction of the 21 entries of J^T J,
 //      the 6 of J^T r, the cost and the valid count gives one FP32 partial
-//      per CTA;
-//   3. a bounded grid barrier;
-//   4. EVERY CTA reduces all partials (FP32, the same fixed order) and runs
-//      the same LM step on its shared-memory copy of the LM state, on one
-//      warp: accept or reject the candidate (mean cost E/N must decrease),
-//      update lambda, solve the damped 6x6 system in FP64 (3x3 block
-//      elimination) and compose the next candidate pose exp(delta) T in FP64.
-//      Identical inputs and code give identical states in all CTAs, so no
-//      broadcast is needed.
+//      per fixed chunk of pixels, written with the evaluation's tag;
+//   3. EVERY CTA reads all partials, each until it carries the tag (this is
+//      the only grid-wide wait, bounded), reduces them (FP32, the same fixed
+//      order) and runs the same LM step on its shared-memory copy of the LM
+//      state, on one warp: accept or reject the candidate (mean cost E/N must
+//      decrease), update lambda, solve the damped 6x6 system and compose the
+//      next candidate pose exp(delta) T (FP32 with exactly formed residuals
+//      and a pose carried as float pairs; see lm_step_warp).  Identical
+//      inputs and code give identical states in all CTAs, so no broadcast is
+//      needed.
 // The LM state never leaves shared memory; a level ends early when the step
-// falls below the thresholds.  Results are deterministic: fixed grid, fixed
+// falls below the thresholds.  Results are deterministic: fixed chunks, fixed
 // pixel-to-thread mapping, fixed reduction order.
 #include <cmath>
 #include <type_traits>
@@ -77,14 +78,19 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
   } else {
     // the cell straddles blocks: the neighbours' pools come from the table
     const int4 n0 = __ldg(v.nbr + 2 * (size_t)pool), n1 = __ldg(v.nbr + 2 * (size_t)pool + 1);
-    const int nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+    const bool ex = lx == 7, ey = ly == 7, ez = lz == 7;
+    int pn[8];
+    bool present = true;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      const int ix = lx + (n & 1), iy = ly + ((n >> 1) & 1), iz = lz + ((n >> 2) & 1);
-      const int slot = (ix >> 3) + 2 * (iy >> 3) + 4 * (iz >> 3);
-      const int pn = nb[slot];
-      if (pn < 0) return false;
-      c[n] = __ldg(words + (size_t)pn * stride + (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7));
+      pn[n] = nbr_pick(n0, n1, (n & 1) && ex, ((n >> 1) & 1) && ey, ((n >> 2) & 1) && ez);
+      present = present && pn[n] >= 0;
+    }
+    if (!present) return false;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const int ix = (lx + (n & 1)) & 7, iy = (ly + ((n >> 1) & 1)) & 7, iz = (lz + ((n >> 2) & 1)) & 7;
+      c[n] = __ldg(words + (size_t)pn[n] * stride + ix + 8 * iy + 64 * iz);
     }
   }
   float F[8];
@@ -126,7 +132,7 @@ __device__ __forceinline__ bool model_sample(const DevVol& v, const DevParams& p
     *colour = ((imax >> 16) & 255u) != 255u;
     if (!*colour) return true;
 #pragma unroll
-    for (int n = 0; n < 8; ++n) In[n] = (float)((c[n] >> 16) & 255u);  // intensities x 254
+    for (int n = 0; n < 8; ++n) In[n] = u2f_exact((c[n] >> 16) & 255u);  // intensities x 254
     iscale = kI8Scale;
   }
   const float d00 = lerpf(In[0], In[1], fx), d10 = lerpf(In[2], In[3], fx);
@@ -184,22 +190,28 @@ __host__ __device__ constexpr int up6(int i, int j) { return i * 6 - i * (i - 1)
 // reciprocal square root (the factor only preconditions the refined solve).
 // False unless every pivot is positive and finite.  Fully unrolled.
 __device__ __forceinline__ bool chol6(float A[21], float inv[6]) {
+  // every loop has constant bounds (with guards) so that it unrolls fully and
+  // A stays in registers
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     float s = A[up6(j, j)];
 #pragma unroll
-    for (int k = 0; k < j; ++k) s = fmaf(-A[up6(k, j)], A[up6(k, j)], s);
+    for (int k = 0; k < 6; ++k)
+      if (k < j) s = fmaf(-A[up6(k, j)], A[up6(k, j)], s);
     ok = ok && (s > 0.0f) && (s < 3.0e38f);
     const float r = rsqrtf(fmaxf(s, 1.0e-30f));
     A[up6(j, j)] = s * r;
     inv[j] = r;
 #pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      float t = A[up6(j, i)];
+    for (int i = 0; i < 6; ++i) {
+      if (i > j) {
+        float t = A[up6(j, i)];
 #pragma unroll
-      for (int k = 0; k < j; ++k) t = fmaf(-A[up6(k, i)], A[up6(k, j)], t);
-      A[up6(j, i)] = t * r;
+        for (int k = 0; k < 6; ++k)
+          if (k < j) t = fmaf(-A[up6(k, i)], A[up6(k, j)], t);
+        A[up6(j, i)] = t * r;
+      }
     }
   }
   return ok;
@@ -211,14 +223,17 @@ __device__ __forceinline__ void chol6_solve(const float A[21], const float inv[6
   for (int i = 0; i < 6; ++i) {
     float t = b[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) t = fmaf(-A[up6(k, i)], b[k], t);
+    for (int k = 0; k < 6; ++k)
+      if (k < i) t = fmaf(-A[up6(k, i)], b[k], t);
     b[i] = t * inv[i];
   }
 #pragma unroll
-  for (int i = 5; i >= 0; --i) {
+  for (int ii = 0; ii < 6; ++ii) {
+    const int i = 5 - ii;
     float t = b[i];
 #pragma unroll
-    for (int k = i + 1; k < 6; ++k) t = fmaf(-A[up6(i, k)], b[k], t);
+    for (int k = 0; k < 6; ++k)
+      if (k > i) t = fmaf(-A[up6(i, k)], b[k], t);
     b[i] = t * inv[i];
   }
 }
@@ -322,9 +337,10 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
   }
   const bool ok = chol6(A, inv);
   chol6_solve(A, inv, d);
-  // residual -g - (H + lambda diag H) d, exact to about 2^-46 (every lane)
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
+  // residual -g - (H + lambda diag H) d, exact to about 2^-46: row i on
+  // lane i, then gathered on every lane
+  {
+    const int i = lane < 6 ? lane : 0;
     float sh = -S.gf[i], sl = 0.0f;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -341,7 +357,9 @@ __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const 
         sl += e - pe - lhe * d[j];
       }
     }
-    r[i] = sh + sl;
+    const float ri = sh + sl;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) r[q] = __shfl_sync(0xffffffffu, ri, q);
   }
   chol6_solve(A, inv, r);
 #pragma unroll
@@ -415,14 +433,90 @@ __device__ __forceinline__ int chunk_pixels(int npix) {
   return npix >= (1 << 18) ? 4 * kRegThreads : (npix >= (1 << 16) ? kRegThreads : kRegThreads / 4);
 }
 constexpr int kMaxPerThread = 4;  // pixels of one chunk per thread (chunk_pixels / kRegThreads at most)
+constexpr int kReduceBatch = 8;   // partials per lane and component loaded at once in the reduction
+
+// The pixels of chunk ch that thread tin of its slot samples (at most
+// kMaxPerThread, kRegThreads apart): raw depth (0 where masked), (u, v) and
+// packed RGB, and the pixel's cached block entry.  All loads are issued
+// before any is used, so their latencies overlap.
+struct PixelRegs {
+  unsigned raw[kMaxPerThread], uv[kMaxPerThread], rgb[kMaxPerThread];
+  unsigned long long cache[kMaxPerThread];
+};
+
+__device__ __forceinline__ void load_pixels(const RegDesc& d, PixelRegs& P, int ch, int chunk, int npix, int nchunks,
+                                            int Ws, unsigned long long magic, int stride, int tin) {
+  const DevFrame& f = d.f;
+  const int end = ch < nchunks ? min(npix, (ch + 1) * chunk) : 0;
+#pragma unroll
+  for (int j = 0; j < kMaxPerThread; ++j) {
+    const int i = ch * chunk + tin + j * kRegThreads;
+    P.raw[j] = 0u;
+    P.uv[j] = 0u;
+    P.rgb[j] = 0u;
+    P.cache[j] = kEmpty;
+    if (i < end) {
+      // row = i / Ws by a reciprocal multiply (off by at most one for
+      // i < 2^32), then one integer correction step
+      int row = (int)(((unsigned long long)i * magic) >> 32);
+      if (row * Ws > i) --row;
+      else if ((row + 1) * Ws <= i) ++row;
+      const int u = (i - row * Ws) * stride, vv = row * stride;
+      const int idx = vv * f.W + u;
+      unsigned raw = __ldg(f.depth + idx);
+      if (d.mask && __ldg(d.mask + idx)) raw = 0u;  // masked: not sampled
+      const uint8_t* cp = f.rgb + 3 * (size_t)idx;
+      P.raw[j] = raw;
+      P.uv[j] = (unsigned)u | ((unsigned)vv << 16);
+      if (raw != 0u && d.pxcache) P.cache[j] = __ldcg(d.pxcache + idx);
+      P.rgb[j] = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
+    }
+  }
+}
+
+// Every CTA of a registration group calls this once, after its last read of
+// the partial sums.  The last CTA to leave clears the arrival count and
+// advances the tag base past the
+// registration's tags (at most 3 + the sum of the level iteration caps); when
+// the tags would reach kTagLimit it first clears the whole partial buffer,
+// whose tags then all read 0, and restarts the base at 0.  Either way every
+// tag left in the buffer is below the next registration's tags.
+__device__ __forceinline__ void leave_registration(const RegDesc& d, int lb, int G, unsigned tag0) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(d.tags + 1, 1u) == (unsigned)G - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  const unsigned span = (unsigned)(d.c.iters[0] + d.c.iters[1] + d.c.iters[2] + 3);
+  unsigned next = tag0 + span;
+  if (next >= kTagLimit - span) {
+    const size_t n = (size_t)2 * 29 * d.max_slots;
+    for (size_t i = threadIdx.x; i < n; i += kRegThreads) d.partials[i] = 0ull;
+    next = 0u;
+  }
+  if (threadIdx.x == 0) {
+    d.tags[2] = 0u;
+    d.tags[1] = 0u;
+    d.tags[0] = next;
+  }
+}
 
 // One whole registration (see the file comment) run by a group of G CTAs,
-// this CTA being number lb of the group.  d.partials: 2 x 29 x max chunks
-// floats (double-buffered by evaluation parity); d.bar: a zeroed counter.
+// this CTA being number lb of the group.
+//
+// Exchange of the partial sums: evaluation e of the registration tags its
+// partials with base + e + 1 (base: d.tags[0]) and then counts the CTA in
+// d.tags[2] with a relaxed reduction; every CTA waits until the count shows
+// all G arrivals of e, then reads the partials, re-polling any word that does
+// not carry the tag yet (no fence orders a CTA's partials before its count,
+// so the tags carry the ordering).  The count also makes double buffering by
+// evaluation parity safe: a CTA writes evaluation e + 2 only after all G CTAs
+// arrived at e + 1, each after it had read all of evaluation e.
 template <int ST>
 __device__ void register_body(const RegDesc& d, int lb, int G) {
   __shared__ LMShared S;
   __shared__ float red[kRegWarps][29];
+  __shared__ int s_arrived;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const DevFrame& f = d.f;
   const DevParams& p = d.p;
@@ -451,24 +545,27 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
     S.Rclf[threadIdx.x] = S.Rlf[threadIdx.x];
   }
   __syncthreads();
+  const unsigned tag0 = ld_relaxed_gpu(d.tags);  // written by the previous registration's last CTA
   int eval = 0;
-  for (int l = 0; l < 3; ++l) {
+  bool failed = false;
+  PixelRegs P;
+  for (int l = 0; l < 3 && !failed; ++l) {
     const int stride = d.c.strides[l];
     const int Ws = (f.W + stride - 1) / stride, Hs = (f.H + stride - 1) / stride;
     const int npix = Ws * Hs;
     const int chunk = chunk_pixels(npix);
     const int nchunks = (npix + chunk - 1) / chunk;
-    // row = i / Ws by a reciprocal multiply (off by at most one for i < 2^32),
-    // then one integer correction step
     const unsigned long long magic = (0x100000000ull + Ws - 1) / Ws;
     const int iters = d.c.iters[l];
+    bool pre = false;  // P holds step 0's pixels of this evaluation
     for (int it = 0; it <= iters; ++it) {
       const int mode = it == 0 ? 0 : 1;
       if (mode == 1 && S.done) break;  // identical decision in every CTA of the group
       const float* Tf = mode == 0 ? S.Rf : S.Rcf;
       const float R0 = Tf[0], R1 = Tf[1], R2 = Tf[2], R3 = Tf[3], R4 = Tf[4], R5 = Tf[5], R6 = Tf[6], R7 = Tf[7],
                   R8 = Tf[8], t0 = Tf[9], t1 = Tf[10], t2 = Tf[11];
-      float* part = d.partials + (size_t)(eval & 1) * 29 * d.max_chunks;
+      unsigned long long* part = d.partials + (size_t)(eval & 1) * 29 * d.max_slots;
+      const unsigned tag = tag0 + (unsigned)eval + 1u;
       // chunks narrower than the CTA run side by side, one per warp group
       // (slot): chunk lb + G (slot + slots it) at step it
       const int width = min(chunk, kRegThreads);  // threads per chunk
@@ -479,50 +576,23 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
         float acc[29];
 #pragma unroll
         for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
-        const int end = ch < nchunks ? min(npix, (ch + 1) * chunk) : 0;
-        // this thread's pixels of the chunk (at most kMaxPerThread): depth,
-        // mask and colour loaded up front, so their latencies overlap; the
-        // samples are then taken in the same order as the pixels
-        unsigned praw[kMaxPerThread], puv[kMaxPerThread], prgb[kMaxPerThread];
-        unsigned long long pcache[kMaxPerThread];
-#pragma unroll
-        for (int j = 0; j < kMaxPerThread; ++j) {
-          const int i = ch * chunk + tin + j * kRegThreads;
-          praw[j] = 0u;
-          puv[j] = 0u;
-          prgb[j] = 0u;
-          pcache[j] = kEmpty;
-          if (i < end) {
-            int row = (int)(((unsigned long long)i * magic) >> 32);
-            if (row * Ws > i) --row;
-            else if ((row + 1) * Ws <= i) ++row;
-            const int u = (i - row * Ws) * stride, vv = row * stride;
-            const int idx = vv * f.W + u;
-            unsigned raw = __ldg(f.depth + idx);
-            if (d.mask && __ldg(d.mask + idx)) raw = 0u;  // masked: not sampled
-            const uint8_t* cp = f.rgb + 3 * (size_t)idx;
-            praw[j] = raw;
-            puv[j] = (unsigned)u | ((unsigned)vv << 16);
-            if (raw != 0u && d.pxcache) pcache[j] = __ldcg(d.pxcache + idx);
-            prgb[j] = (unsigned)__ldg(cp) | ((unsigned)__ldg(cp + 1) << 8) | ((unsigned)__ldg(cp + 2) << 16);
-          }
-        }
+        if (!(step == 0 && pre)) load_pixels(d, P, ch, chunk, npix, nchunks, Ws, magic, stride, tin);
 #pragma unroll 1
         for (int j = 0; j < kMaxPerThread; ++j) {
           // the next pixel's values rotate into slot 0 (registers, no local memory)
-          const unsigned raw = praw[0], uvj = puv[0], rgbj = prgb[0];
-          const unsigned long long cj = pcache[0];
+          const unsigned raw = P.raw[0], uvj = P.uv[0], rgbj = P.rgb[0];
+          const unsigned long long cj = P.cache[0];
 #pragma unroll
           for (int r = 0; r + 1 < kMaxPerThread; ++r) {
-            praw[r] = praw[r + 1];
-            puv[r] = puv[r + 1];
-            prgb[r] = prgb[r + 1];
-            pcache[r] = pcache[r + 1];
+            P.raw[r] = P.raw[r + 1];
+            P.uv[r] = P.uv[r + 1];
+            P.rgb[r] = P.rgb[r + 1];
+            P.cache[r] = P.cache[r + 1];
           }
           if (!pixel_valid(p, raw)) continue;
           const int u = (int)(uvj & 0xFFFFu), vv = (int)(uvj >> 16);
-          const float D = (float)raw * p.inv_depth_scale;
-          const float x = ((float)u - f.cx) * f.ifx * D, y = ((float)vv - f.cy) * f.ify * D;
+          const float D = u2f_exact(raw) * p.inv_depth_scale;
+          const float x = (u2f_exact((unsigned)u) - f.cx) * f.ifx * D, y = (u2f_exact((unsigned)vv) - f.cy) * f.ify * D;
           const float px = R0 * x + R1 * y + R2 * D + t0;
           const float py = R3 * x + R4 * y + R5 * D + t1;
           const float pz = R6 * x + R7 * y + R8 * D + t2;
@@ -563,30 +633,61 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
           if (lane < 29) red[warp][lane] = v[0];
         }
         __syncthreads();
-        // the chunk partial of each slot: its warps' sums in order
+        // the chunk partial of each slot: its warps' sums in order, tagged
         if (warp < slots && lane < 29) {
           const int cs = lb + G * (warp + slots * step);
           if (cs < nchunks) {
             const int wpc = width / 32;
             float sv = 0.0f;
             for (int w = 0; w < wpc; ++w) sv += red[warp * wpc + w][lane];
-            part[lane * nchunks + cs] = sv;
+            st_relaxed_gpu_u64(part + lane * nchunks + cs, ((unsigned long long)tag << 32) | __float_as_uint(sv));
           }
         }
         __syncthreads();
       }
-      if (!grid_sync_counter(d.bar, (unsigned)(eval + 1) * (unsigned)G + d.bar_extra, d.status, d.spin_limit))
-        return;
+      // arrival: one relaxed count per CTA (the step loop ended with a CTA
+      // barrier after this CTA's partial stores)
+      if (threadIdx.x == 0) red_relaxed_gpu_add(d.tags + 2, 1u);
+      // the next evaluation of this level samples the same pixels: their
+      // loads are issued now and complete while the CTA waits for the others
+      pre = it < iters;
+      if (pre) load_pixels(d, P, lb + G * slot, chunk, npix, nchunks, Ws, magic, stride, tin);
+      if (threadIdx.x == 0)
+        s_arrived = await_count(d.tags + 2, (unsigned)(eval + 1) * (unsigned)G + d.bar_extra, d.spin_limit);
+      __syncthreads();
+      if (!s_arrived) {
+        if (threadIdx.x == 0) atomicOr(d.status, ST_BARRIER);
+        failed = true;
+        break;
+      }
       // every CTA of the group: FP32 reduction of the chunk partials in a fixed
-      // order (lane-strided sums, then a shuffle tree); L1 bypassed
+      // order (lane-strided sums, then a shuffle tree); a word without this
+      // evaluation's tag is read again until it has it
+      bool ok = true;
       {
         const int ca = warp, cb = warp + kRegWarps;  // warp w: components w and w + 16
-        const float* ra = part + ca * nchunks;
-        const float* rb = part + (cb < 29 ? cb : ca) * nchunks;
+        const unsigned long long* ra = part + ca * nchunks;
+        const unsigned long long* rb = part + (cb < 29 ? cb : ca) * nchunks;
         float fa = 0.0f, fb = 0.0f;
-        for (int k = lane; k < nchunks; k += 32) {
-          fa += __ldcg(ra + k);
-          fb += __ldcg(rb + k);
+        for (int k0 = lane; k0 < nchunks && ok; k0 += 32 * kReduceBatch) {
+          // the loads of a batch are issued together (one L2 round trip),
+          // then checked and added in order
+          unsigned long long va[kReduceBatch], vb[kReduceBatch];
+#pragma unroll
+          for (int u = 0; u < kReduceBatch; ++u) {
+            const int k = k0 + 32 * u;
+            va[u] = k < nchunks ? ld_relaxed_gpu_u64(ra + k) : 0ull;
+            vb[u] = k < nchunks ? ld_relaxed_gpu_u64(rb + k) : 0ull;
+          }
+#pragma unroll
+          for (int u = 0; u < kReduceBatch; ++u) {
+            const int k = k0 + 32 * u;
+            if (k < nchunks) {
+              ok = ok && await_tag(ra + k, va[u], tag, d.spin_limit) && await_tag(rb + k, vb[u], tag, d.spin_limit);
+              fa += __uint_as_float((unsigned)va[u]);
+              fb += __uint_as_float((unsigned)vb[u]);
+            }
+          }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -598,12 +699,18 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
           if (cb < 29) S.redf[cb] = fb;
         }
       }
-      __syncthreads();
+      if (!__syncthreads_and(ok)) {  // some wait ran out: leave, reporting it once per CTA
+        if (threadIdx.x == 0) atomicOr(d.status, ST_BARRIER);
+        failed = true;
+        break;
+      }
       if (warp == 0) lm_step_warp(S, mode, l, it == iters, d.c, lane);
       __syncthreads();
       ++eval;
     }
   }
+  leave_registration(d, lb, G, tag0);
+  if (failed) return;
   if (lb == 0) {
     if (threadIdx.x < 16) {  // the pose in FP64: hi + lo of each entry, the last row 0 0 0 1
       const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
@@ -681,8 +788,8 @@ RegDesc make_reg_desc(rf_volume* vol, const DevFrame& f, const double* T_init, c
     d.c.strides[l] = vol->p.lm_strides[l];
   }
   d.partials = vol->d_partials;
-  d.max_chunks = vol->max_chunks;
-  d.bar = vol->d_regbar;
+  d.max_slots = vol->max_slots;
+  d.tags = vol->d_regtags;
   d.status = vol->d_status;
   d.spin_limit = vol->wait_spins;
   d.bar_extra = vol->wait_extra;
@@ -706,8 +813,6 @@ static rf_status launch_coop(rf_volume* vol, const void* fn, int grid, void** ar
 rf_status launch_track(rf_volume* vol, const DevFrame& f, const double* T_init, const uint8_t* mask, double* T_out,
                        rf_track_info* info, cudaStream_t st) {
   RegDesc d = make_reg_desc(vol, f, T_init, mask, T_out, info);
-  rf_status s = check_cuda(vol, cudaMemsetAsync(vol->d_regbar, 0, 2 * sizeof(unsigned), st), "barrier reset");
-  if (s != RF_OK) return s;
   void* args[] = {&d};
   const void* fn = vol->p.storage == RF_STORAGE_FP16 ? (const void*)k_register<RF_STORAGE_FP16>
                                                      : (const void*)k_register<RF_STORAGE_FP32>;

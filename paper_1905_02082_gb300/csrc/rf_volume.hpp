@@ -33,9 +33,13 @@ struct rf_volume {
   unsigned* d_status = nullptr;
 
   // registration scratch
-  float* d_partials = nullptr;  // 2 x 29 x max_chunks floats (also the mesh counter)
-  int max_chunks = 0;
-  unsigned* d_regbar = nullptr;  // grid-barrier words of the registration kernel
+  // 2 x 29 x max_slots tagged partial sums of the registration (tag << 32 |
+  // float bits).  Mesh extraction and virtual-depth filling reuse word 0 as a
+  // counter between registrations: a count below 2^32 in it, or in its low
+  // half, leaves a tag no later registration waits for.
+  unsigned long long* d_partials = nullptr;
+  int max_slots = 0;
+  unsigned* d_regtags = nullptr;  // registration tag base and leaving count
   int reg_grid = 0;
 
   // mask scratch

@@ -91,6 +91,7 @@ SIGNATURES = [
     ("rf_get_launch_config", _int, [_vp, C.POINTER(rf_launch_config)]),
     ("rf_set_launch_config", _int, [_vp, C.POINTER(rf_launch_config)]),
     ("rf_set_wait_limits", _int, [_vp, _i64, _int]),
+    ("rf_set_registration_tag_base", _int, [_vp, C.c_uint32]),
     ("rf_batch_create", _int, [_vp, _int, C.POINTER(_vp)]),
     ("rf_batch_destroy", _int, [_vp]),
     ("rf_batch_process", _int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -396,9 +397,13 @@ class Volume:
         _check(load().rf_set_launch_config(self.h, C.byref(cfg)), self.h)
 
     def set_wait_limits(self, spin_limit: int = 0, extra_arrivals: int = 0):
-        """Bound of every grid-barrier wait (0: the default, about one second);
+        """Bound of every grid-wide wait (0: the default, about one second);
         extra_arrivals > 0 makes every wait run out (tests of the error path)."""
         _check(load().rf_set_wait_limits(self.h, int(spin_limit), int(extra_arrivals)), self.h)
+
+    def set_registration_tag_base(self, base: int):
+        """Next base of the registration's tag sequence (tests of its restart)."""
+        _check(load().rf_set_registration_tag_base(self.h, int(base)), self.h)
 
     def set_profiling(self, enable: bool):
         _check(load().rf_set_profiling(self.h, 1 if enable else 0), self.h)

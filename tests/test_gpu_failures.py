@@ -1,9 +1,11 @@
 """Bounded failure paths of the library, each made to happen without any GPU
 fault: a flood fill capped below the sweeps it needs, a frustum candidate list
 too small for the frame, a pose beyond the hash key range, a mesh buffer too
-small for the surface, and grid barriers whose waits run out (fault injection
-through rf_set_wait_limits: the barrier waits for arrivals that never come,
-gives up after a short, bounded number of polls, and the kernel returns).
+small for the surface, and grid-wide waits that run out (fault injection
+through rf_set_wait_limits: the flood fill's barrier waits for arrivals that
+never come, the registration for partial sums with a tag no evaluation
+writes; each gives up after a short, bounded number of polls, and the kernel
+returns).  Also the restart of the registration's tag sequence.
 Every error is read back through rf_sync_status (or the call's return code),
 and the volume keeps working afterwards.
 """
@@ -141,12 +143,14 @@ def test_mesh_buffer_too_small(R):
 
 
 @pytest.mark.parametrize("stage", ["registration", "flood fill"])
-def test_grid_barrier_waits_run_out_and_are_reported(R, stage):
-    """Fault injection on the bounded grid barriers: with one extra arrival
-    expected that never comes, every CTA's wait runs out after 2^14 polls (no
-    sleeps below 4,096 polls and 64 ns after: well under 10 ms), the kernel
-    returns, the status reads RF_ERR_NOT_CONVERGED, and with the injection
-    removed the same call succeeds and gives the normal result."""
+def test_grid_wide_waits_run_out_and_are_reported(R, stage):
+    """Fault injection on the bounded grid-wide waits (the flood fill's
+    barrier expects one arrival more than there are CTAs; the registration
+    waits for a tag that no evaluation writes): every CTA's wait runs out
+    after 2^14 polls (no sleeps below 4,096 polls and 64 ns after: well under
+    10 ms), the kernel returns, the status reads RF_ERR_NOT_CONVERGED, and
+    with the injection removed the same call succeeds and gives the normal
+    result."""
     cam = CAM_QVGA
     T = look_at([0.45, 0.32, 1.31], TARGET)
     d, rgb, _ = render_frame([ROOM, BOX], cam, T)
@@ -167,10 +171,35 @@ def test_grid_barrier_waits_run_out_and_are_reported(R, stage):
     with pytest.raises(R.RFError) as e:
         vol.sync()
     elapsed = time.perf_counter() - t0
-    assert e.value.status == NOT_CONVERGED and "barrier" in str(e.value)
+    assert e.value.status == NOT_CONVERGED and "grid-wide wait" in str(e.value)
     assert elapsed < 2.0
     vol.set_wait_limits(0, 0)
     again = run()
     vol.sync()
     np.testing.assert_array_equal(again.cpu().numpy(), good.cpu().numpy())
+    vol.close()
+
+
+def test_registration_tag_sequence_restarts(R):
+    """The registration's tags restart at 0 (the partial-sum buffer cleared)
+    before they would reach 2^31; a registration right at the limit, the one
+    after the restart and one from an arbitrary base all give the pose of a
+    registration from the initial base, bit for bit, without an error."""
+    cam = CAM_QVGA
+    T = look_at([0.45, 0.32, 1.31], TARGET)
+    d, rgb, _ = render_frame([ROOM, BOX], cam, T)
+    vol = _room_volume(R)
+    fr = _dev(R, vol, d, rgb, cam)
+    ref, _ = vol.track(fr, T)
+    vol.sync()
+    span = 3 + 10 + 5 + 5  # 3 + the default iteration caps
+    limit = (1 << 31) - 1 - span
+    with pytest.raises(R.RFError):
+        vol.set_registration_tag_base(limit + 1)
+    for base in (limit, None, 12345):
+        if base is not None:
+            vol.set_registration_tag_base(base)
+        out, _ = vol.track(fr, T)
+        vol.sync()
+        np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
     vol.close()
