@@ -65,8 +65,14 @@ DevFrame make_dev_frame(const rf_frame* f) {
 }
 
 void prof_record(rf_volume* vol, int ev, cudaStream_t st) {
-  // External records stay event-record nodes when captured into a graph.
-  if (vol->profiling) cudaEventRecordWithFlags(vol->ev[ev], st, cudaEventRecordExternal);
+  if (!vol->profiling) return;
+  // External records stay event-record nodes when captured into a graph;
+  // outside a capture the flag is refused, so a plain record is taken there.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(vol->ev[ev], st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(vol->ev[ev], st);
 }
 
 bool frame_ok(const rf_volume* vol, const rf_frame* f) {
@@ -505,9 +511,6 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
                                              offsetof(BatchStage, mode));
     desc[i] = make_reg_desc(v, f[i], v->d_T, nullptr, v->d_T + 16, nullptr);
     desc[n + i] = make_reg_desc(v, f[i], v->d_T + 16, v->d_mask, v->d_T + 32, v->d_info);
-    // no pixel block cache in batches: with many streams its traffic evicts
-    // the models from L2 (it changes no result)
-    desc[i].pxcache = desc[n + i].pxcache = nullptr;
   }
   std::vector<FloodDesc> flood(n);
   std::vector<MaskDesc> mdesc(n);
@@ -515,7 +518,6 @@ rf_status batch_capture(rf_batch* b, const rf_frame* frames, const std::vector<d
     rf_volume* v = b->vols[i];
     flood[i] = make_flood_desc(v, f[i]);
     mdesc[i] = make_mask_desc(v, f[i], v->d_T + 16, v->d_mask);
-    mdesc[i].pxcache = nullptr;  // batches keep no pixel block cache
   }
   e = cudaMalloc(&out->d_desc, sizeof(RegDesc) * desc.size());
   if (e == cudaSuccess) e = cudaMemcpy(out->d_desc, desc.data(), sizeof(RegDesc) * desc.size(), cudaMemcpyHostToDevice);
@@ -703,6 +705,8 @@ rf_status rf_create_volume(const rf_params* p, int64_t n_buckets, int64_t max_bl
   if (vol->ff_grid < 1) vol->ff_grid = 1;
   s = clear_model(vol, 0);
   if (!s) s = check_cuda(vol, cudaMemset(vol->d_status, 0, sizeof(unsigned)), "status reset");
+  // the frustum search's ticket counter starts at 0
+  if (!s) s = check_cuda(vol, cudaMemset(vol->d_integ, 0, sizeof(IntegState)), "integration state reset");
   // registration tags start at 0 (base, counts) with every partial-sum word's tag 0
   if (!s) s = check_cuda(vol, cudaMemset(vol->d_regtags, 0, 3 * sizeof(unsigned)), "tag reset");
   if (!s)

@@ -14,9 +14,9 @@
 // rounding verified with int64 products after a float guess.
 //
 // Kernels, in stream order:
-//   k_integ_prep   quantise the pose, reset counters                 (1 thread)
-//   k_tilemax      16x16-tile maximum of valid unmasked depth        (tile/CTA)
-//   k_integ_aabb   block range of the truncated frustum              (1 thread)
+//   k_frustum      16x16-tile maximum of valid unmasked depth        (tile/CTA),
+//                  then in its last CTA: quantised pose, counters reset,
+//                  block range of the truncated frustum
 //   k_cull         conservative per-block frustum/depth test, warp-aggregated
 //                  append to the candidate list                     (block/thread)
 //   k_integrate    exact per-voxel predicate, lock-free hash insert of blocks
@@ -29,12 +29,16 @@
 namespace rf {
 namespace {
 
-// Quantised pose (one entry per lane: conversions run on the FP64 pipe, so
-// they are spread over lanes), the per-frame constants of the voxel loop and
-// the reset of the per-frame counters.
-__global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const int* __restrict__ n_blocks,
-                             DevParams p, const int* gate) {
-  if (gated_off(gate, kModeFirst)) return;
+// Largest frustum search region (blocks); beyond it the frame is rejected
+// with RF_ERR_OUT_OF_RANGE (d_max / voxel_size far too large, or a
+// non-finite pose).
+constexpr long long kMaxSearchBlocks = 1ll << 28;
+
+// Quantised pose (one entry per lane of warp 0: conversions run on the FP64
+// pipe, so they are spread over lanes), the per-frame constants of the voxel
+// loop and the reset of the per-frame counters.
+__device__ __forceinline__ void integ_prep(const double* __restrict__ T, IntegState* st, const int* __restrict__ n_blocks,
+                                           const DevParams& p, int max_um) {
   const int a = threadIdx.x;
   if (a < 9) {
     const int i = a / 3, j = a % 3;
@@ -44,10 +48,9 @@ __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const
     st->tq[a - 9] = llround(T[(a - 9) * 4 + 3] * 1e6);
     st->t[a - 9] = (float)T[(a - 9) * 4 + 3];
   } else if (a == 12) {
-    st->max_um = -1;
+    st->max_um = max_um;
     st->n_cand = 0;
     st->work = 0;
-    st->total = 0;
     st->clipped = 0;
     st->new_blocks = 0;
     st->updated = 0ull;
@@ -59,50 +62,17 @@ __global__ void k_integ_prep(const double* __restrict__ T, IntegState* st, const
   }
 }
 
-// Per 16x16 tile: the largest valid unmasked depth (frustum search), and the
-// frame's depth with invalid and masked pixels zeroed (the per-voxel loop
-// then tests one value per pixel).
-__global__ void __launch_bounds__(256) k_tilemax(DevFrame f, DevParams p, const uint8_t* __restrict__ mask,
-                                                 int* __restrict__ tilemax, IntegState* st, int tiles_x,
-                                                 uint16_t* __restrict__ dm) {
-  if (gated_off(f.gate, kModeFirst)) return;
-  const int tile = blockIdx.x;
-  const int u = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
-  const int v = (tile / tiles_x) * kTile + (threadIdx.x / kTile);
-  int d = -1;
-  if (u < f.W && v < f.H) {
-    const int idx = v * f.W + u;
-    const unsigned raw = f.depth[idx];
-    const bool use = pixel_valid(p, raw) && !(mask && mask[idx]);
-    if (use) d = (int)(raw * p.du_um);
-    dm[idx] = use ? (uint16_t)raw : (uint16_t)0;
-  }
-  d = __reduce_max_sync(0xffffffffu, d);
-  __shared__ int s[8];
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = d;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int m = s[0];
-    for (int w = 1; w < 8; ++w) m = max(m, s[w]);
-    tilemax[tile] = m;
-    if (m >= 0) atomicMax(&st->max_um, m);
-  }
-}
-
-// Largest frustum search region (blocks); beyond it the frame is rejected
-// with RF_ERR_OUT_OF_RANGE (d_max / voxel_size far too large, or a
-// non-finite pose).
-constexpr long long kMaxSearchBlocks = 1ll << 28;
-
 // Block range of the truncated frustum z in (z_near, zfar], zfar =
 // min(max valid depth + tau, d_max), over the pixel rectangle.  Float math on
-// 8 lanes (one frustum corner each); the 2-voxel margin covers its rounding.
-__global__ void k_integ_aabb(const double* __restrict__ T, DevFrame f, DevParams p, IntegState* st) {
-  if (gated_off(f.gate, kModeFirst)) return;
-  const int lane = threadIdx.x;
-  const int max_um = st->max_um;
+// 8 lanes of one warp (one frustum corner each); the 2-voxel margin covers
+// its rounding.  R, t: the pose as floats (already in st).
+__device__ __forceinline__ void integ_aabb(const DevFrame& f, const DevParams& p, IntegState* st, int max_um,
+                                           int lane) {
   if (max_um < 0) {
-    if (lane == 0) st->total = 0;
+    if (lane == 0) {
+      st->total = 0;
+      st->zfar = 0.0f;
+    }
     return;
   }
   const float zfar = fminf((float)max_um * 1e-6f + p.tau, (float)p.dmax_um * 1e-6f);
@@ -151,6 +121,57 @@ __global__ void k_integ_aabb(const double* __restrict__ T, DevFrame f, DevParams
   st->total = total > 0 ? total : 0;
   st->zfar = zfar;
   st->clipped = clipped ? 1 : 0;  // blocks beyond the key range cannot be stored (reported by k_cull)
+}
+
+// Frustum search, first kernel of an integration.  Per 16x16 tile: the
+// largest valid unmasked depth, and the frame's depth with invalid and masked
+// pixels zeroed (the per-voxel loop then tests one value per pixel).  The
+// last CTA to finish (a ticket counter it resets) then takes the maximum over
+// the tiles and writes the quantised pose, the per-frame constants, the reset
+// counters and the block range of the truncated frustum.
+__global__ void __launch_bounds__(256) k_frustum(DevFrame f, DevParams p, const uint8_t* __restrict__ mask,
+                                                 int* __restrict__ tilemax, IntegState* st, int tiles_x, int ntiles,
+                                                 uint16_t* __restrict__ dm, const double* __restrict__ T,
+                                                 const int* __restrict__ n_blocks) {
+  if (gated_off(f.gate, kModeFirst)) return;
+  const int tile = blockIdx.x;
+  const int u = (tile % tiles_x) * kTile + (threadIdx.x % kTile);
+  const int v = (tile / tiles_x) * kTile + (threadIdx.x / kTile);
+  int d = -1;
+  if (u < f.W && v < f.H) {
+    const int idx = v * f.W + u;
+    const unsigned raw = f.depth[idx];
+    const bool use = pixel_valid(p, raw) && !(mask && mask[idx]);
+    if (use) d = (int)(raw * p.du_um);
+    dm[idx] = use ? (uint16_t)raw : (uint16_t)0;
+  }
+  d = __reduce_max_sync(0xffffffffu, d);
+  __shared__ int s[8];
+  __shared__ int s_last;
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = s[0];
+    for (int w = 1; w < 8; ++w) m = max(m, s[w]);
+    tilemax[tile] = m;
+    __threadfence();  // the tile maximum before the ticket
+    s_last = atomicAdd(&st->ticket, 1u) == (unsigned)ntiles - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  int m = -1;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) m = max(m, __ldcg(tilemax + t));
+  m = __reduce_max_sync(0xffffffffu, m);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+  __syncthreads();
+  int max_um = s[0];
+  for (int w = 1; w < 8; ++w) max_um = max(max_um, s[w]);
+  if (threadIdx.x < 32) integ_prep(T, st, n_blocks, p, max_um);
+  if (threadIdx.x == 0) st->ticket = 0u;
+  __syncthreads();  // R and t in st are visible to the whole CTA
+  if (threadIdx.x >= 32 && threadIdx.x < 64) integ_aabb(f, p, st, max_um, threadIdx.x - 32);
 }
 
 // Conservative test: may keep blocks without updated voxels, never drops one.
@@ -753,10 +774,8 @@ rf_status launch_nbr_fixup(rf_volume* vol, const int* lo_ptr, int lo, cudaStream
 // The frustum search of an integration: prep, tile maxima, AABB, cull.
 static rf_status launch_frustum(rf_volume* vol, const DevFrame& f, const double* T, const uint8_t* mask, cudaStream_t st) {
   const int tiles_x = (f.W + kTile - 1) / kTile, tiles_y = (f.H + kTile - 1) / kTile;
-  k_integ_prep<<<1, 32, 0, st>>>(T, vol->d_integ, vol->d_nblocks, vol->dp, f.gate);
-  k_tilemax<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x,
-                                               vol->d_dmask);
-  k_integ_aabb<<<1, 32, 0, st>>>(T, f, vol->dp, vol->d_integ);
+  k_frustum<<<tiles_x * tiles_y, 256, 0, st>>>(f, vol->dp, mask, vol->d_tilemax, vol->d_integ, tiles_x,
+                                               tiles_x * tiles_y, vol->d_dmask, T, vol->d_nblocks);
   k_cull<<<vol->sm_count * vol->launch.cull_ctas_per_sm, 256, 0, st>>>(f, vol->dp, vol->d_integ, vol->d_tilemax, tiles_x, tiles_y, vol->d_cand,
                                             vol->p.max_candidates, vol->d_status);
   return check_cuda(vol, cudaGetLastError(), "frustum launch");

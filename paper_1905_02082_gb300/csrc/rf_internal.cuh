@@ -151,6 +151,7 @@ struct IntegState {
   int work;
   int new_blocks;
   int pool_before;  // pool size when the integration started (new blocks follow it)
+  unsigned ticket;  // CTAs of the frustum search that have finished (reset by the last)
   unsigned long long updated;
   // constant of the per-voxel loop: one voxel step along world z in camera
   // coordinates, as a float estimate in ticks

@@ -515,7 +515,7 @@ __device__ __forceinline__ void leave_registration(const RegDesc& d, int lb, int
 template <int ST>
 __device__ void register_body(const RegDesc& d, int lb, int G) {
   __shared__ LMShared S;
-  __shared__ float red[kRegWarps][29];
+  __shared__ float red[2][kRegWarps][29];  // per-warp sums of a chunk, double-buffered by step parity
   __shared__ int s_arrived;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const DevFrame& f = d.f;
@@ -557,7 +557,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
     const int nchunks = (npix + chunk - 1) / chunk;
     const unsigned long long magic = (0x100000000ull + Ws - 1) / Ws;
     const int iters = d.c.iters[l];
-    bool pre = false;  // P holds step 0's pixels of this evaluation
+    bool pre = false;  // P already holds the pixels of the next step to run
     for (int it = 0; it <= iters; ++it) {
       const int mode = it == 0 ? 0 : 1;
       if (mode == 1 && S.done) break;  // identical decision in every CTA of the group
@@ -576,7 +576,7 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
         float acc[29];
 #pragma unroll
         for (int i = 0; i < 29; ++i) acc[i] = 0.0f;
-        if (!(step == 0 && pre)) load_pixels(d, P, ch, chunk, npix, nchunks, Ws, magic, stride, tin);
+        if (!pre) load_pixels(d, P, ch, chunk, npix, nchunks, Ws, magic, stride, tin);
 #pragma unroll 1
         for (int j = 0; j < kMaxPerThread; ++j) {
           // the next pixel's values rotate into slot 0 (registers, no local memory)
@@ -630,23 +630,28 @@ __device__ void register_body(const RegDesc& d, int lb, int G) {
               v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
             }
           }
-          if (lane < 29) red[warp][lane] = v[0];
+          if (lane < 29) red[step & 1][warp][lane] = v[0];
         }
+        // the next step's pixels: loads issued now, used after the partials
+        pre = lb + G * slots * (step + 1) < nchunks;
+        if (pre) load_pixels(d, P, ch + G * slots, chunk, npix, nchunks, Ws, magic, stride, tin);
         __syncthreads();
-        // the chunk partial of each slot: its warps' sums in order, tagged
+        // the chunk partial of each slot: its warps' sums in order, tagged.
+        // No barrier after it: the next step writes the other buffer, and
+        // this one again only after the next step's barrier, which these
+        // reads precede.
         if (warp < slots && lane < 29) {
           const int cs = lb + G * (warp + slots * step);
           if (cs < nchunks) {
             const int wpc = width / 32;
             float sv = 0.0f;
-            for (int w = 0; w < wpc; ++w) sv += red[warp * wpc + w][lane];
+            for (int w = 0; w < wpc; ++w) sv += red[step & 1][warp * wpc + w][lane];
             st_relaxed_gpu_u64(part + lane * nchunks + cs, ((unsigned long long)tag << 32) | __float_as_uint(sv));
           }
         }
-        __syncthreads();
       }
-      // arrival: one relaxed count per CTA (the step loop ended with a CTA
-      // barrier after this CTA's partial stores)
+      // arrival: one relaxed count per CTA (other warps' partial stores may
+      // still be on their way: the readers check the tags)
       if (threadIdx.x == 0) red_relaxed_gpu_add(d.tags + 2, 1u);
       // the next evaluation of this level samples the same pixels: their
       // loads are issued now and complete while the CTA waits for the others

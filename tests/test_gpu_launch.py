@@ -54,3 +54,33 @@ def test_launch_shapes_do_not_change_results(R):
         np.testing.assert_array_equal(filled, outs[0][2])
         for k in ("coords", "F", "W", "rgb", "wc"):
             np.testing.assert_array_equal(snap[k], outs[0][1][k])
+
+
+def test_profiling_times_whole_frames_and_standalone_integration(R):
+    """rf_set_profiling: the whole-frame call (a captured graph) and a
+    standalone integration (no capture) both record their device times, and
+    profiling changes no result."""
+    seq = make_sequence("tiny", 6, n_frames=4)
+    cam = seq.camera
+    plain, prof = P.gpu_volume(R, cam, 0.02, tune=False), P.gpu_volume(R, cam, 0.02, tune=False)
+    prof.set_profiling(True)
+    T = {id(plain): None, id(prof): None}
+    for i in range(3):
+        d, rgb, Tg, _ = seq.frame(i)
+        for vol in (plain, prof):
+            Tn, _ = vol.process(P.dev_frame(R, vol, d, rgb, cam), Tg if T[id(vol)] is None else T[id(vol)])
+            vol.sync()
+            T[id(vol)] = Tn.cpu().numpy()
+        np.testing.assert_array_equal(T[id(plain)], T[id(prof)])
+    p = prof.profile()
+    assert p.frame_ms > 0 and p.track_ms[0] > 0 and p.integrate_kernel_ms > 0
+    d, rgb, Tg, _ = seq.frame(3)
+    for vol in (plain, prof):
+        vol.integrate(P.dev_frame(R, vol, d, rgb, cam), Tg)
+        vol.sync()
+    assert prof.profile().integrate_kernel_ms > 0
+    a, b = plain.export(), prof.export()
+    for k in ("coords", "F", "W", "rgb", "wc"):
+        np.testing.assert_array_equal(a[k], b[k])
+    plain.close()
+    prof.close()
