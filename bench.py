@@ -50,6 +50,7 @@ def _render(args):
 
 
 MAX_RENDERED = 300  # the static configuration's length; longer runs play it back and forth
+PRECISION_RENDERED = 120  # distinct frames of the precision sequence; longer runs play them back and forth
 
 
 def frame_order(n_rendered: int, n: int):
@@ -254,7 +255,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FOOTPRINT = os.path.join(ROOT, "tests", "golden", "track_footprint_static.json")
 # DRAM bytes (read + write) per launch on this workload from one ncu capture of the
 # kernel as it stands (None once the kernel has changed since its capture).
-REGISTER_DRAM_BYTES = None
+REGISTER_DRAM_BYTES = 7.148288e6 + 7.936e3
 INTEGRATE_DRAM_BYTES = 37.397248e6 + 54.528e3
 
 
@@ -411,19 +412,22 @@ def _render_precision(args):
     return make_sequence("precision", 0, n_frames=n).frame(i)[:3]
 
 
-def run_precision(R, frames, dev, stream, flush, warmup):
+def run_precision(R, frames, order, dev, stream, flush, warmup):
     """The precision configuration (1280x720, voxel 0.5 cm, tau 5 cm, 2^22
     buckets) through rf_process_frame, FP16 storage and FP32 storage on the
     same frames: frames/s and per-frame latency of each (same timing rules as
     the headline loop), and the FP16 form's drift from the FP32 form (pose
-    difference per frame; the TSDF difference on the blocks both hold)."""
+    difference per frame; the TSDF difference on the blocks both hold).
+    order: the rendered frame used at each step (a sequence longer than the
+    rendered frames plays them back and forth)."""
     import torch
     from synth.scenes import CAM_HD as cam
     K = R.Intrinsics(cam.fx, cam.fy, cam.cx, cam.cy)
     d_depth = [torch.from_numpy(f[0].astype(np.int32)).to(dev).to(torch.uint16).contiguous() for f in frames]
     d_rgb = [torch.from_numpy(f[1]).to(dev).contiguous() for f in frames]
-    out = {"workload": f"precision configuration: {len(frames)} frames of 1280x720 (fx=fy=1050), voxel 0.5 cm, "
-                       "tau 5 cm, 2^22 buckets", "frames": len(frames)}
+    out = {"workload": f"precision configuration: {len(order)} frames of 1280x720 (fx=fy=1050; {len(frames)} "
+                       "rendered, played back and forth), voxel 0.5 cm, tau 5 cm, 2^22 buckets",
+           "frames": len(order), "rendered": len(frames)}
     poses, snaps = {}, {}
     for name, storage in (("fp16", R.STORAGE_FP16), ("fp32", R.STORAGE_FP32)):
         vol = R.Volume(n_buckets=1 << 22, max_blocks=1_500_000, max_width=cam.width, max_height=cam.height,
@@ -431,11 +435,11 @@ def run_precision(R, frames, dev, stream, flush, warmup):
         T = torch.as_tensor(frames[0][2], device=dev).contiguous()
         Tn = torch.empty_like(T)
         ms, P = [], []
-        for i in range(len(frames)):
+        for i, k in enumerate(order):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            R.rf_process_frame(vol.h, vol.frame(d_depth[i], d_rgb[i], K), T, Tn, None, None, stream)
+            R.rf_process_frame(vol.h, vol.frame(d_depth[k], d_rgb[k], K), T, Tn, None, None, stream)
             b.record(stream)
             T, Tn = Tn, T
             b.synchronize()
@@ -452,7 +456,7 @@ def run_precision(R, frames, dev, stream, flush, warmup):
     dt = [float(np.linalg.norm(a[:3, 3] - b[:3, 3])) for a, b in zip(poses["fp16"], poses["fp32"])]
     dr = [float(np.arccos(np.clip((np.trace(a[:3, :3] @ b[:3, :3].T) - 1) / 2, -1, 1)))
           for a, b in zip(poses["fp16"], poses["fp32"])]
-    gt = [float(np.linalg.norm(a[:3, 3] - f[2][:3, 3])) for a, f in zip(poses["fp16"], frames)]
+    gt = [float(np.linalg.norm(a[:3, 3] - frames[k][2][:3, 3])) for a, k in zip(poses["fp16"], order)]
     ka = {tuple(c): i for i, c in enumerate(snaps["fp16"]["coords"])}
     kb = {tuple(c): i for i, c in enumerate(snaps["fp32"]["coords"])}
     common = [c for c in ka if c in kb]
@@ -592,11 +596,12 @@ def main():
         return
 
     workers = max(1, min(16, (os.cpu_count() or 1) // world))  # ranks share the host cores
-    pframes = []
+    pframes, porder = [], []
     if rank == 0 and args.precision_frames > 0:
+        nr = min(args.precision_frames, PRECISION_RENDERED)
+        porder = frame_order(nr, args.precision_frames)
         with mp.get_context("spawn").Pool(workers) as pool:
-            pframes = pool.map(_render_precision, [(i, args.precision_frames) for i in range(args.precision_frames)],
-                               chunksize=1)
+            pframes = pool.map(_render_precision, [(i, nr) for i in range(nr)], chunksize=1)
     if args.only == "precision":
         import torch
         torch.cuda.set_device(local)
@@ -605,7 +610,7 @@ def main():
         import paper_1905_02082_gb300.refusion as R
         dev = torch.device("cuda", local)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        prec = run_precision(R, pframes, dev, torch.cuda.current_stream(), flush, min(10, args.warmup))
+        prec = run_precision(R, pframes, porder, dev, torch.cuda.current_stream(), flush, min(10, args.warmup))
         print(json.dumps({"precision": prec}))
         return
     n_frames = min(args.warmup + args.steps, MAX_RENDERED)
@@ -768,9 +773,9 @@ def main():
 
     # kernels of this library per whole frame (graph nodes): one cooperative
     # launch per registration (2), mask: seeds, erosion, flood fill,
-    # dilation (4), integration: prep, tile maxima, frustum, cull, update,
-    # neighbour tables (6)
-    launches_per_frame = 2 + 4 + 6
+    # dilation (4), integration: frustum search, cull, update, neighbour
+    # tables (4)
+    launches_per_frame = 2 + 4 + 4
     batch = None
     batch_fp16 = None
     if args.batch_streams > 0:
@@ -779,7 +784,7 @@ def main():
     single_fp16 = run_single(R, frames, K, cam, dev, stream, flush, args, storage=R.STORAGE_FP16)
     virtual_depth = run_virtual_depth(R, frames, K, cam, dev, stream, args) if args.vd_frames > 0 else None
     serving = run_serving(R, splan, clips, args) if splan else None
-    precision = run_precision(R, pframes, dev, stream, flush, 4) if pframes else None
+    precision = run_precision(R, pframes, porder, dev, stream, flush, 4) if pframes else None
 
     if rank == 0:
         st = vol.stats()
