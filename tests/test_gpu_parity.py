@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from synth import make_sequence
-from synth.scenes import CAM_TINY, CAM_VGA, Camera, Prim
+from synth.scenes import CAM_QVGA, CAM_TINY, CAM_VGA, Camera, Prim
 
 from ._scenes import ROOM, corner_pose, render_frame, rot_err
 
@@ -122,6 +122,24 @@ def test_integration_with_mask_and_ragged_frame(R, O):
         vol.sync()
         orc.integrate(orc_frame(O, d, rgb, cam), T, mask)
     assert_volumes_match(vol.export(), orc.export())
+
+
+def test_integration_frames_of_changing_size(R, O):
+    """One volume sized for 640x480 integrates frames of 161x97, 640x480 and
+    320x240 in turn (the frustum search's tile count and its last-CTA ticket
+    change from call to call); every result equals the oracle's."""
+    cams = (Camera(161, 97, 131.5, 129.0, 80.5, 47.0), CAM_VGA, CAM_QVGA)
+    vol = R.Volume(n_buckets=1 << 14, max_blocks=60000, max_width=640, max_height=480, voxel_size=0.02, trunc=TAU)
+    orc = O.OracleVolume(voxel_size=0.02, trunc=TAU)
+    for k, cam in enumerate(cams * 2):
+        T = corner_pose(k % 3)
+        d, rgb, _ = render_frame([ROOM], cam, T, noise="quadratic", seed=10 + k)
+        vol.integrate(dev_frame(R, vol, d, rgb, cam), T)
+        vol.sync()
+        orc.integrate(orc_frame(O, d, rgb, cam), T)
+        if k in (0, 2, 5):
+            assert_volumes_match(vol.export(), orc.export())
+    vol.close()
 
 
 def test_integration_empty_and_invalid_frames(R, O):
