@@ -281,9 +281,9 @@ __device__ __forceinline__ bool prod_less(float a, unsigned na, float b, unsigne
 //   FP64 solve for the systems met here (condition numbers ~10^2);
 //   exp(d) - I = [A K + B K^2 | rho + B K rho + C K^2 rho] in FP32 (its
 //   entries are of the order of the step, so FP32 is relative to the step);
-//   the candidate pose Tc = T + (exp(d) - I) T: the increment in FP32, the sum
-//   in FP64 (one FP64 add per entry, lanes 0-11 in parallel), and its float
-//   copy for the next evaluation.
+//   the candidate pose Tc = T + (exp(d) - I) T: the increment in FP32, added
+//   to the pose carried as float pairs with an error-free sum (lanes 0-11 in
+//   parallel); the pair's high float is what the next evaluation uses.
 __device__ void lm_step_warp(LMShared& S, int mode, int level, bool last, const LMConst& c, int lane) {
   const float Enf = S.redf[27];
   const long long Nn = (long long)(S.redf[28] + 0.5f);
