@@ -709,8 +709,9 @@ def main():
     roof_reg = {"bound": "hbm", "kernel": "k_register (one registration: 3 levels, all LM evaluations)",
                 "achieved": reg_gbs, "peak": peak, "unit": "GB/s", "frac": reg_gbs / peak,
                 "traffic": REGISTER_DRAM_BYTES,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (null: the kernel "
-                                  "changed since the last capture)",
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                   "(profiles/k_register_static_640x480.md)" if REGISTER_DRAM_BYTES is not None else
+                                   "null: the kernel changed since its last ncu capture"),
                 "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs), of " + peak_kind,
                 "bytes_per_launch": reg_bytes,
                 "bytes_source": "oracle-counted footprint: 5 B per pixel (+1 B mask) + 8 B per distinct voxel read + "
@@ -724,7 +725,9 @@ def main():
     roof_int = {"bound": "hbm", "kernel": "k_integrate (per-voxel TSDF/colour update)",
                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": INTEGRATE_DRAM_BYTES,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                   "(profiles/k_integrate_static_640x480.md)" if INTEGRATE_DRAM_BYTES is not None else
+                                   "null: the kernel changed since its last ncu capture"),
                 "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs), of " + peak_kind,
                 "bytes_per_launch": statistics.mean(bytes_per),
                 "bytes_source": "18 B per updated voxel + 4.5 KB per new block + 2 B per pixel of masked depth",
@@ -799,30 +802,30 @@ def main():
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "mean": statistics.mean(step_ms)},
             "stages_ms": stage,
+            "e2e": e2e,
+            "gpu_launches": launches_per_frame * args.steps,
+            "gpu_launches_per_frame": launches_per_frame,
+            "clocks": clk,
             "roofline": dominant,
-            "roofline_register": roof_reg,
             "roofline_integrate": roof_int,
             "frame_hbm": {"achieved": frame_gbs, "peak": peak, "unit": "GB/s", "frac": frame_gbs / peak,
                           "bytes_per_frame": statistics.mean(frame_bytes),
                           "bytes_source": "5 B per pixel input + both registrations' model reads + 1 B per pixel "
                                           "mask + the integration's bytes"},
+            "cpu_baseline": cpu,
+            "batch": batch,
+            "batch_fp16": batch_fp16,
+            "single_fp16": single_fp16,
             "tracking": {"rmse_m": float(np.sqrt(np.mean(np.square(errs)))), "max_m": float(np.max(errs)),
                          "note": "free-running pose vs the ground truth of the timed frames (no loop closure)"},
             "work": {"updated_voxels": statistics.mean(upd), "new_blocks": statistics.mean(newb),
                      "candidates": statistics.mean(p.candidates for p in profs), "blocks": st.n_blocks,
                      "guard_pixels": statistics.mean(p.guard_pixels for p in profs)},
-            "batch": batch,
-            "batch_fp16": batch_fp16,
-            "single_fp16": single_fp16,
-            "virtual_depth": virtual_depth,
-            "serving": serving,
-            "precision": precision,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches_per_frame * args.steps,
-            "gpu_launches_per_frame": launches_per_frame,
-            "clocks": clk,
+            "roofline_register": roof_reg,
             "wall_s_timed": wall,
+            "virtual_depth": virtual_depth,
+            "precision": precision,
+            "serving": serving,
         }
         print(json.dumps(line))
     vol.close()
