@@ -86,8 +86,9 @@ typedef struct rf_params {
  * weight and an 8-bit intensity (round(254 I), Sec. III-B) in one 4-byte
  * tracking word, colour and colour weight in a 4-byte colour word (8 B per
  * voxel); tracking reads 4 B per trilinear corner and free-space carving
- * rewrites 4 B per voxel.  Per-pixel maths and reductions are FP32 and the
- * LM solve FP64 in both modes; hash indexing and the mask's decisions stay
+ * rewrites 4 B per voxel.  Per-pixel maths, reductions and the LM step are
+ * FP32 in both modes (the step's refinement residual formed exactly, the
+ * pose carried as float pairs); hash indexing and the mask's decisions stay
  * exact (on the values stored).  rf_volume_export returns F = FP16 value x
  * tau (float multiply); rf_volume_import rounds F / tau to FP16 (nearest). */
 #define RF_STORAGE_FP32 0
@@ -124,7 +125,7 @@ typedef struct rf_profile {
   float frame_ms;            /* device time of the last rf_process_frame* call */
   float track_ms[2];         /* first and second registration */
   float mask_ms;             /* seeds, erosion, flood fill, dilation */
-  float integrate_ms;        /* integration stage: pose quantisation, tile maxima, frustum, cull, update */
+  float integrate_ms;        /* integration stage: frustum search, cull, update, neighbour tables */
   float integrate_kernel_ms; /* the per-voxel update kernel alone */
   int64_t candidates;        /* frustum candidate blocks of the last integration */
   int64_t updated_voxels;    /* voxels updated by the last integration */
