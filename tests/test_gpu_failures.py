@@ -2,10 +2,10 @@
 fault: a flood fill capped below the sweeps it needs, a frustum candidate list
 too small for the frame, a pose beyond the hash key range, a mesh buffer too
 small for the surface, and grid-wide waits that run out (fault injection
-through rf_set_wait_limits: the flood fill's barrier waits for arrivals that
-never come, the registration for partial sums with a tag no evaluation
-writes; each gives up after a short, bounded number of polls, and the kernel
-returns).  Also the restart of the registration's tag sequence.
+through rf_set_wait_limits: the flood fill's barrier and the registration's
+arrival count each wait for one arrival more than there are CTAs, which
+never comes; each wait gives up after a short, bounded number of polls, and
+the kernel returns).  Also the restart of the registration's tag sequence.
 Every error is read back through rf_sync_status (or the call's return code),
 and the volume keeps working afterwards.
 """
@@ -145,12 +145,11 @@ def test_mesh_buffer_too_small(R):
 @pytest.mark.parametrize("stage", ["registration", "flood fill"])
 def test_grid_wide_waits_run_out_and_are_reported(R, stage):
     """Fault injection on the bounded grid-wide waits (the flood fill's
-    barrier expects one arrival more than there are CTAs; the registration
-    waits for a tag that no evaluation writes): every CTA's wait runs out
-    after 2^14 polls (no sleeps below 4,096 polls and 64 ns after: well under
-    10 ms), the kernel returns, the status reads RF_ERR_NOT_CONVERGED, and
-    with the injection removed the same call succeeds and gives the normal
-    result."""
+    barrier and the registration's arrival count each expect one arrival
+    more than there are CTAs): every CTA's wait runs out after 2^14 polls (no
+    sleeps below 4,096 polls and 64 ns after), the kernel returns, the status
+    reads RF_ERR_NOT_CONVERGED, and with the injection removed the same call
+    succeeds and gives the normal result."""
     cam = CAM_QVGA
     T = look_at([0.45, 0.32, 1.31], TARGET)
     d, rgb, _ = render_frame([ROOM, BOX], cam, T)
